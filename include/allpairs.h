@@ -1,0 +1,221 @@
+/*
+ * allpairs.h -- C ABI of the GB300 all-pairs library (libap.so).
+ *
+ * The library evaluates a pair function f(l(i), l(j)) for every unordered pair
+ * 0 <= i < j < n of an item set (the problem statement of Sec. III), walking
+ * the strict upper triangle in recursively blocked tiles (Sec. IV-B) with
+ * persistent CUDA kernels that pop tiles from an atomic queue.
+ *
+ * General conventions
+ *   - All compute is asynchronous on the caller's CUDA stream (`stream` is a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - The caller owns every input and output buffer.  The library owns what
+ *     ap_create_items allocates and frees it in ap_destroy.
+ *   - Arguments are validated before any launch: an error return leaves no
+ *     partial write in caller memory.  Errors are returned as ap_status and
+ *     never thrown across the ABI.
+ *   - Packed pair layout: results for pair (i, j), i < j, live at
+ *         p(i, j) = i*n - i*(i+1)/2 + (j - i - 1),     P = n(n-1)/2 entries,
+ *     the row-major enumeration of the strict upper triangle.  n < 2 gives
+ *     P = 0 and every call returns AP_OK without touching memory.
+ *   - One handle is not thread-safe; different handles are independent.
+ *   - Device waits inside the kernels are bounded; when one runs out the
+ *     kernel records a code readable with ap_last_device_error() and the call
+ *     that synchronises next reports AP_ERR_TIMEOUT.
+ */
+#ifndef ALLPAIRS_H
+#define ALLPAIRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AP_OK = 0,
+  AP_ERR_INVALID_ARG = 1,  /* bad pointer, size, kind or combination */
+  AP_ERR_OOM = 2,          /* a device or pinned-host allocation failed */
+  AP_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed */
+  AP_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+  AP_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+  AP_ERR_STATE = 6         /* handle in the wrong state for the call */
+} ap_status;
+
+typedef enum {
+  AP_ITEMS_CLOUD2D = 0,    /* weighted 2-D point clouds (microscopy particles, Sec. V-C) */
+  AP_ITEMS_CLOUD3D = 1,    /* weighted 3-D point clouds */
+  AP_ITEMS_VECTOR = 2      /* dense FP32 vectors of one length (noise patterns, Sec. V-A) */
+} ap_item_kind;
+
+typedef enum {
+  /* Gaussian overlap cost between point clouds, the cross term of the GMM
+   * L2 distance (Sec. V-C):
+   *   f(i,j) = sum_a sum_b w_a w_b exp(-|x_a - (R x_b + t)|^2 / (2(s_a^2 + s_b^2)))
+   * output float[P] */
+  AP_FN_OVERLAP = 0,
+  /* Pearson (normalised cross) correlation of dense vectors (Sec. V-A):
+   *   r(i,j) = sum_k (x_ik - mu_i)(x_jk - mu_j) / sqrt(ss_i ss_j)
+   * output double[P] */
+  AP_FN_PEARSON = 1,
+  /* debugging pair function: atomically adds 1 to int32 out[p(i,j)] for every
+   * pair the schedule visits (coverage check: every i < j exactly once).
+   * Works for any item kind; the caller zeroes out[] first. */
+  AP_FN_COVERAGE = 2
+} ap_pair_fn;
+
+typedef enum {
+  AP_PREC_FP32 = 0,        /* plain FP32 CUDA-core path */
+  AP_PREC_SPLIT_BF16 = 1   /* Pearson Gram as hi*hi + hi*lo + lo*hi BF16 products
+                              on the tensor cores, FP32 accumulation */
+} ap_precision;
+
+typedef struct ap_items ap_items;   /* opaque, library-owned */
+
+/* Description of an item set (the inputs of the load pipeline l, Sec. III). */
+typedef struct ap_items_desc {
+  int32_t kind;            /* ap_item_kind */
+  int32_t data_on_host;    /* 1: x/y/z/sigma/weight/data are host pointers; 0: device */
+  int64_t n_items;         /* n >= 0 */
+  /* Point clouds (kind CLOUD2D/CLOUD3D), ragged structure-of-arrays.
+   * offsets is ALWAYS a host pointer, int64[n_items + 1], non-decreasing,
+   * offsets[0] == 0; the points of item i are [offsets[i], offsets[i+1]).
+   * x, y, sigma: float[offsets[n]]; z: float[offsets[n]] for 3-D, ignored
+   * for 2-D; weight: float[offsets[n]] or NULL (all weights 1).  sigma > 0,
+   * weight >= 0 (zero-weight points contribute nothing).  Empty items are
+   * allowed (their costs are 0). */
+  const int64_t *offsets;
+  const float *x, *y, *z, *sigma, *weight;
+  /* Dense vectors (kind VECTOR): row-major float[n_items][ld], dim <= ld
+   * values per row are used, dim >= 2. */
+  const float *data;
+  int64_t dim;
+  int64_t ld;              /* row stride in elements; 0 means ld = dim */
+  /* Vector representations to build, a bitmask of (1u << ap_precision);
+   * 0 selects split-BF16 only. */
+  uint32_t precisions;
+  /* Vectors on the host only: 0 = copy everything to the device at creation
+   * (the host buffer may be freed afterwards); > 0 = out-of-core mode, the
+   * library keeps `data` (which must be page-locked and outlive the handle)
+   * and streams items through an HBM slot cache of at most this many bytes
+   * (the first-level device cache of Sec. IV-A). */
+  uint64_t slot_cache_bytes;
+} ap_items_desc;
+
+/* Run statistics of the last ap_run_pairs on a handle. */
+typedef struct ap_run_stats {
+  int64_t tiles;            /* tiles executed */
+  int64_t item_loads;       /* item loads into the device cache (R * n in Sec. VI-A) */
+  double reuse_R;           /* loads relative to the data set size, Eq. 1 */
+  uint64_t h2d_bytes;       /* bytes copied host -> device */
+  double slot_hit_rate;     /* fraction of item requests served by a resident slot */
+  int32_t tile_m, tile_n;   /* tile shape used (items x items) */
+  int32_t order;            /* 0 = recursive quadrant order, 1 = row panels */
+  int32_t reserved;
+} ap_run_stats;
+
+/*
+ * ap_create_items -- run the load pipeline l(i) for every item (Sec. III:
+ * transfer to the GPU and pre-process there) into library-owned storage.
+ *   Clouds: points are padded per item to a multiple of 4 with zero weight
+ *   and stored as (x, y[, z], sigma^2, log2 w) in device memory.
+ *   Vectors: per item mu_i and ss_i in FP64 (two passes), then the centred
+ *   rows c = x - mu_i, stored as BF16 hi = rn(c), lo = rn(c - hi) for
+ *   split-BF16 and/or as FP32 c for the FP32 path, rows padded with zeros.
+ * Inputs may be freed when the call returns (after a stream synchronise),
+ * except the out-of-core host source (see slot_cache_bytes).
+ * Errors: AP_ERR_INVALID_ARG (desc/out NULL, negative sizes, bad kind,
+ * offsets not non-decreasing, missing arrays), AP_ERR_OOM, AP_ERR_CUDA.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+ap_status ap_create_items(const ap_items_desc *desc, void *stream, ap_items **out);
+
+/*
+ * ap_update_items -- re-run the load pipeline for vectors of the same shape
+ * into the existing storage (no allocation).  data: row-major
+ * float[n_items][ld] on the host (data_on_host = 1) or the device.
+ * Errors: AP_ERR_INVALID_ARG, AP_ERR_STATE (not a resident vector set).
+ */
+ap_status ap_update_items(ap_items *items, const float *data, int32_t data_on_host,
+                          void *stream);
+
+/*
+ * ap_run_pairs -- f(l(i), l(j)) for every pair i < j (Sec. III), written to
+ * the packed device array `out` (layout above).
+ *   fn = AP_FN_OVERLAP: clouds; out float[P]; params NULL (identity) or a
+ *        device float[P][3] = (theta, tx, ty) per pair (2-D only), the
+ *        transform applied to the second item j.
+ *   fn = AP_FN_PEARSON: vectors; out double[P]; precision selects the Gram
+ *        path (the representation must have been built at creation).
+ *   fn = AP_FN_COVERAGE: any kind; out int32[P] is incremented.
+ * Errors: AP_ERR_INVALID_ARG (fn/kind mismatch, NULL out with P > 0, params
+ * with 3-D clouds), AP_ERR_STATE (representation not built), AP_ERR_CUDA,
+ * AP_ERR_TIMEOUT.
+ */
+ap_status ap_run_pairs(ap_items *items, int32_t fn, int32_t precision,
+                       const float *params, void *out, void *stream);
+
+/*
+ * ap_backward -- adjoint of the overlap cost (2-D clouds) with respect to the
+ * per-pair transform (theta, tx, ty):
+ *   grad_params[p][k] = grad_out[p] * d f_p / d param_k,
+ *   d f / d t     = sum w_a w_b e d / s2,
+ *   d f / d theta = sum w_a w_b e (d . J R x_b) / s2,  J = [[0,-1],[1,0]],
+ * with d = x_a - (R x_b + t), s2 = s_a^2 + s_b^2, e = exp(-|d|^2 / (2 s2)),
+ * the exponentials recomputed rather than stored.  params: device float[P][3]
+ * or NULL (identity); grad_out: device float[P] or NULL (all ones);
+ * grad_params: device float[P][3], overwritten; f_out: device float[P] or NULL.
+ * Errors: AP_ERR_INVALID_ARG (not 2-D clouds, grad_params NULL with P > 0).
+ */
+ap_status ap_backward(ap_items *items, const float *params, const float *grad_out,
+                      float *grad_params, float *f_out, void *stream);
+
+/*
+ * ap_ascent -- batched per-pair registration: n_steps fused steps of
+ *   (f, g) = (f, grad f)(params);  if f >= fmin: params += eta * g / f
+ * (gradient ascent on log f) for every pair at once.  params: device
+ * float[P][3], updated in place; f_out: device float[P] or NULL, receives f
+ * at the parameters of the last step (before its update); flags: device
+ * int32[P] or NULL, set to 1 where some step was skipped (f < fmin).
+ * Errors: AP_ERR_INVALID_ARG (not 2-D clouds, n_steps < 0, params NULL).
+ */
+ap_status ap_ascent(ap_items *items, float *params, int32_t n_steps, float eta,
+                    float fmin, float *f_out, int32_t *flags, void *stream);
+
+/* ap_destroy -- free everything the handle owns; NULL is accepted.  Waits for
+ * the handle's outstanding work on its streams first. */
+ap_status ap_destroy(ap_items *items);
+
+/* Statistics of the last ap_run_pairs (host struct, caller-owned). */
+ap_status ap_get_stats(const ap_items *items, ap_run_stats *out);
+
+/* Static, NUL-terminated description of a status code. */
+const char *ap_status_string(ap_status s);
+
+/* Code recorded by a bounded device wait that ran out during the handle's
+ * last synchronised call (0 = none); also cleared by this call. */
+int32_t ap_last_device_error(ap_items *items);
+
+/* n(n-1)/2 (Sec. VI-A); 0 for n < 2. */
+int64_t ap_pair_count(int64_t n);
+
+/* Packed index of (i, j), 0 <= i < j < n; -1 otherwise. */
+int64_t ap_pair_index(int64_t i, int64_t j, int64_t n);
+
+/*
+ * ap_plan_tiles -- host-side tile list of the schedule: the upper triangle of
+ * an n x n item grid cut into square blocks of `block` items, the block pairs
+ * (I, J) with I <= J listed in recursive quadrant order (Sec. IV-B: split into
+ * four quadrants, recurse, skip empty quadrants).  Writes (I, J) pairs to
+ * out[2k], out[2k+1] for k < *n_tiles when cap suffices.
+ * Errors: AP_ERR_INVALID_ARG (n < 0, block < 1, n_tiles NULL, out NULL with
+ * cap > 0); *n_tiles is always set to the required count.
+ */
+ap_status ap_plan_tiles(int64_t n, int32_t block, int32_t *out, int64_t cap,
+                        int64_t *n_tiles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALLPAIRS_H */

@@ -1,0 +1,250 @@
+"""Thin Python binding of libap.so (the C ABI in include/allpairs.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream, ctypes passes raw pointers and sizes; every step of the all-pairs
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+``lib()`` raises if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libap.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "allpairs.h")
+
+# ap_status
+AP_OK, AP_ERR_INVALID_ARG, AP_ERR_OOM, AP_ERR_CUDA, AP_ERR_TIMEOUT, AP_ERR_UNSUPPORTED, \
+    AP_ERR_STATE = range(7)
+# ap_item_kind
+AP_ITEMS_CLOUD2D, AP_ITEMS_CLOUD3D, AP_ITEMS_VECTOR = range(3)
+# ap_pair_fn
+AP_FN_OVERLAP, AP_FN_PEARSON, AP_FN_COVERAGE = range(3)
+# ap_precision
+AP_PREC_FP32, AP_PREC_SPLIT_BF16 = range(2)
+
+
+class ItemsDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("data_on_host", ctypes.c_int32),
+                ("n_items", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("weight", ctypes.c_void_p),
+                ("data", ctypes.c_void_p), ("dim", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("precisions", ctypes.c_uint32), ("slot_cache_bytes", ctypes.c_uint64)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int64), ("item_loads", ctypes.c_int64),
+                ("reuse_R", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64),
+                ("slot_hit_rate", ctypes.c_double), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class APError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libap.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libap.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        sig = {
+            "ap_create_items": (i32, [ctypes.POINTER(ItemsDesc), vp, ctypes.POINTER(vp)]),
+            "ap_update_items": (i32, [vp, vp, i32, vp]),
+            "ap_run_pairs": (i32, [vp, i32, i32, vp, vp, vp]),
+            "ap_backward": (i32, [vp, vp, vp, vp, vp, vp]),
+            "ap_ascent": (i32, [vp, vp, i32, f32, f32, vp, vp, vp]),
+            "ap_destroy": (i32, [vp]),
+            "ap_get_stats": (i32, [vp, ctypes.POINTER(RunStats)]),
+            "ap_status_string": (ctypes.c_char_p, [i32]),
+            "ap_last_device_error": (i32, [vp]),
+            "ap_pair_count": (i64, [i64]),
+            "ap_pair_index": (i64, [i64, i64, i64]),
+            "ap_plan_tiles": (i32, [i64, i32, vp, i64, ctypes.POINTER(i64)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/allpairs.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ap_[a-z_]+)\s*\(", text)))
+
+
+def status_string(s: int) -> str:
+    return lib().ap_status_string(int(s)).decode()
+
+
+def check(status: int, what: str):
+    if status != AP_OK:
+        raise APError(status, what)
+
+
+def pair_count(n: int) -> int:
+    return int(lib().ap_pair_count(int(n)))
+
+
+def pair_index(i: int, j: int, n: int) -> int:
+    return int(lib().ap_pair_index(int(i), int(j), int(n)))
+
+
+def plan_tiles(n: int, block: int):
+    """Upper-triangle block pairs (I, J) in recursive quadrant order (host)."""
+    import numpy as np
+    cnt = ctypes.c_int64(0)
+    check(lib().ap_plan_tiles(int(n), int(block), None, 0, ctypes.byref(cnt)), "ap_plan_tiles")
+    out = np.empty(2 * max(cnt.value, 1), np.int32)
+    check(lib().ap_plan_tiles(int(n), int(block), out.ctypes.data, cnt.value, ctypes.byref(cnt)),
+          "ap_plan_tiles")
+    return out[:2 * cnt.value].reshape(-1, 2)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Items:
+    """A library-owned item set (``ap_items*``)."""
+
+    def __init__(self, handle, kind: int, n: int):
+        self._h = handle
+        self.kind = kind
+        self.n = n
+        self.P = n * (n - 1) // 2 if n >= 2 else 0
+        self._keep = []
+
+    # ---- construction -------------------------------------------------
+    @classmethod
+    def from_clouds(cls, clouds: dict, device: str = "cuda", stream=None) -> "Items":
+        """Clouds dict (numpy or torch): dim, offsets, x, y, z, sigma, weight."""
+        import numpy as np
+        import torch
+        dim = int(clouds["dim"])
+        off = np.ascontiguousarray(np.asarray(clouds["offsets"]), dtype=np.int64)
+        n = len(off) - 1
+
+        def dev(a):
+            if a is None:
+                return None
+            t = torch.as_tensor(np.asarray(a) if not torch.is_tensor(a) else a)
+            return t.to(device=device, dtype=torch.float32).contiguous()
+
+        arrs = {k: dev(clouds.get(k)) for k in ("x", "y", "z", "sigma", "weight")}
+        if dim != 3:
+            arrs["z"] = None
+        d = ItemsDesc()
+        d.kind = AP_ITEMS_CLOUD3D if dim == 3 else AP_ITEMS_CLOUD2D
+        d.data_on_host = 0
+        d.n_items = n
+        d.offsets = off.ctypes.data
+        for k, t in arrs.items():
+            setattr(d, k, None if t is None else t.data_ptr())
+        h = ctypes.c_void_p()
+        check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
+              "ap_create_items")
+        torch.cuda.synchronize()
+        return cls(h, d.kind, n)
+
+    @classmethod
+    def from_vectors(cls, X, precisions=(AP_PREC_SPLIT_BF16,), stream=None) -> "Items":
+        """X: torch float32 [n, D] on the GPU, or on the host (ideally pinned)."""
+        import torch
+        assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+        d = ItemsDesc()
+        d.kind = AP_ITEMS_VECTOR
+        d.data_on_host = 0 if X.is_cuda else 1
+        d.n_items = X.shape[0]
+        d.data = X.data_ptr()
+        d.dim = X.shape[1]
+        d.ld = X.stride(0)
+        d.precisions = sum(1 << p for p in precisions)
+        h = ctypes.c_void_p()
+        check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
+              "ap_create_items")
+        return cls(h, AP_ITEMS_VECTOR, X.shape[0])
+
+    def update(self, X, stream=None):
+        check(lib().ap_update_items(self._h, _ptr(X), 0 if X.is_cuda else 1, _stream_ptr(stream)),
+              "ap_update_items")
+
+    # ---- compute ------------------------------------------------------
+    def run_pairs(self, fn: int = None, precision: int = AP_PREC_SPLIT_BF16, params=None,
+                  out=None, stream=None):
+        import torch
+        if fn is None:
+            fn = AP_FN_PEARSON if self.kind == AP_ITEMS_VECTOR else AP_FN_OVERLAP
+        if out is None:
+            dt = {AP_FN_OVERLAP: torch.float32, AP_FN_PEARSON: torch.float64,
+                  AP_FN_COVERAGE: torch.int32}[fn]
+            out = (torch.zeros if fn == AP_FN_COVERAGE else torch.empty)(
+                max(self.P, 1), dtype=dt, device="cuda")
+        check(lib().ap_run_pairs(self._h, fn, precision, _ptr(params), _ptr(out),
+                                 _stream_ptr(stream)), "ap_run_pairs")
+        return out[:self.P]
+
+    def backward(self, params=None, grad_out=None, f_out=None, stream=None):
+        import torch
+        g = torch.empty(max(self.P, 1), 3, dtype=torch.float32, device="cuda")
+        if f_out is None:
+            f_out = torch.empty(max(self.P, 1), dtype=torch.float32, device="cuda")
+        check(lib().ap_backward(self._h, _ptr(params), _ptr(grad_out), _ptr(g), _ptr(f_out),
+                                _stream_ptr(stream)), "ap_backward")
+        return g[:self.P], f_out[:self.P]
+
+    def ascent(self, params, n_steps: int, eta: float, fmin: float = 1e-30, stream=None):
+        import torch
+        f = torch.empty(max(self.P, 1), dtype=torch.float32, device="cuda")
+        flags = torch.zeros(max(self.P, 1), dtype=torch.int32, device="cuda")
+        check(lib().ap_ascent(self._h, _ptr(params), int(n_steps), float(eta), float(fmin),
+                              _ptr(f), _ptr(flags), _stream_ptr(stream)), "ap_ascent")
+        return params, f[:self.P], flags[:self.P]
+
+    def stats(self) -> dict:
+        st = RunStats()
+        check(lib().ap_get_stats(self._h, ctypes.byref(st)), "ap_get_stats")
+        return {k: getattr(st, k) for k, _ in RunStats._fields_}
+
+    def last_device_error(self) -> int:
+        return int(lib().ap_last_device_error(self._h))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            check(lib().ap_destroy(self._h), "ap_destroy")
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,172 @@
+// ap_internal.h -- internal declarations of the all-pairs library.
+//
+// Storage kept by a handle, the launch wrappers of each kernel family and the
+// host planners.  Nothing here is part of the C ABI (see allpairs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "allpairs.h"
+
+namespace ap {
+
+// ---------------------------------------------------------------------------
+// status word written by bounded device waits (AP device error codes)
+// ---------------------------------------------------------------------------
+enum DeviceError : int32_t {
+  DEV_OK = 0,
+  DEV_TIMEOUT_FULL = 1,     // consumer gave up waiting for a stage to fill
+  DEV_TIMEOUT_EMPTY = 2,    // producer gave up waiting for a stage to drain
+  DEV_TIMEOUT_ACCUM = 3,    // epilogue gave up waiting for the accumulator
+  DEV_TIMEOUT_STAGE = 4,    // a bulk copy of item data did not land
+  DEV_TIMEOUT_SLOT = 5,     // a slot-ready flag was never raised
+};
+
+// wall-clock budget of one device wait (nanoseconds, %globaltimer)
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;   // 2 s
+
+// ---------------------------------------------------------------------------
+// packed upper-triangle index, p(i,j) = i*n - i(i+1)/2 + (j-i-1)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t pair_index(int64_t i, int64_t j, int64_t n) {
+  return i * n - (i * (i + 1)) / 2 + (j - i - 1);
+}
+
+// ---------------------------------------------------------------------------
+// point-cloud storage: items sorted by the planner, padded to a multiple of
+// 4 points; 2-D points packed as float4 {x, y, s2k, lw}, 3-D as
+// float4 {x, y, z, s2k} plus float lw[], where s2k = sigma^2 / (log2(e)/2)
+// and lw = log2(weight) (-inf for padding), so that
+//   w_b * exp(-d^2 / (2 (sa^2 + sb^2))) = 2^(lw_b - d^2 / (s2k_a + s2k_b)).
+// ---------------------------------------------------------------------------
+struct CloudStore {
+  int dim = 2;
+  int64_t n = 0;
+  bool unit_weights = true;
+  std::vector<int64_t> h_size;      // points per item (original order)
+  std::vector<int32_t> h_perm;      // storage position -> original item id
+  std::vector<int64_t> h_poff;      // padded offsets in storage order [n+1]
+  int64_t total_pts = 0;            // padded
+  float4 *d_pts = nullptr;          // [total_pts]
+  float *d_lw = nullptr;            // [total_pts] (3-D with weights only)
+  int64_t *d_poff = nullptr;        // [n+1]
+  int32_t *d_cnt = nullptr;         // [n] real points per stored item
+  int32_t *d_perm = nullptr;        // [n]
+  // tile plan (rebuilt when the tuned parameters change)
+  int32_t block_items = 0, block_pts = 0, reg_r = 0;
+  bool sorted = false;
+  std::vector<int32_t> h_bstart;    // block b = storage items [bstart[b], bstart[b+1])
+  int32_t *d_bstart = nullptr;
+  int32_t *d_tiles = nullptr;       // [n_tiles][2] block pairs (I <= J)
+  int64_t n_tiles = 0;
+  int64_t tiles_cap = 0;
+};
+
+// ---------------------------------------------------------------------------
+// dense-vector storage
+// ---------------------------------------------------------------------------
+struct VecStore {
+  int64_t n = 0, D = 0, ld = 0;
+  int64_t Dp = 0;                   // padded row length (multiple of 64)
+  uint32_t precisions = 0;
+  double *d_mu = nullptr, *d_ss = nullptr, *d_rs = nullptr;   // FP64 per item
+  __nv_bfloat16 *d_hi = nullptr, *d_lo = nullptr;              // [n][Dp]
+  float *d_c32 = nullptr;                                      // [n][Dp]
+  float *d_stage = nullptr;         // raw rows staged from the host
+  int64_t stage_rows = 0;
+  // out-of-core mode
+  bool out_of_core = false;
+  const float *h_src = nullptr;
+  uint64_t slot_cache_bytes = 0;
+  // tile plans
+  int32_t *d_tiles_tc = nullptr;  int64_t n_tiles_tc = 0;
+  int32_t *d_tiles_f32 = nullptr; int64_t n_tiles_f32 = 0;
+  void *tmap_hi = nullptr, *tmap_lo = nullptr;   // CUtensorMap (host copies)
+  double *d_g64 = nullptr;          // FP64 partial sums of the tensor-core Gram
+};
+
+}  // namespace ap
+
+struct ap_items {
+  int32_t kind = 0;
+  int device = 0;
+  ap::CloudStore cl;
+  ap::VecStore vec;
+  int32_t *d_status = nullptr;      // [0] device error code, [1..] scratch
+  int32_t *d_queue = nullptr;       // tile-queue heads (one per launch slot)
+  float *d_scratch = nullptr;       // generic scratch
+  int64_t scratch_bytes = 0;
+  ap_run_stats stats{};
+  int32_t last_dev_error = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+};
+
+namespace ap {
+
+// ---------------------------------------------------------------------------
+// host planners (plan.cpp)
+// ---------------------------------------------------------------------------
+// Upper-triangle block pairs (I <= J) of an nb x nb block grid in recursive
+// quadrant order (split in four, recurse, skip empty quadrants).
+void dc_block_pairs(int64_t nb, std::vector<int32_t> &out);
+// Group storage-ordered items into blocks of at most max_items items and
+// max_pts padded points (an item larger than max_pts forms its own block).
+// Blocks also respect max_chunks = sum over items of ceil(cnt / chunk).
+void make_blocks(const std::vector<int64_t> &poff, const std::vector<int64_t> &cnt,
+                 int32_t max_items, int64_t max_pts, int64_t chunk, int64_t max_chunks,
+                 std::vector<int32_t> &bstart);
+
+// ---------------------------------------------------------------------------
+// kernel launchers
+// ---------------------------------------------------------------------------
+// vectors (vec.cu)
+cudaError_t launch_vec_stats(const float *X, int64_t n, int64_t D, int64_t ld,
+                             double *mu, double *ss, double *rs, cudaStream_t s);
+cudaError_t launch_vec_split(const float *X, int64_t n, int64_t D, int64_t ld, int64_t Dp,
+                             const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                             float *c32, cudaStream_t s);
+cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
+                            const int32_t *tiles, int64_t n_tiles, int32_t *queue,
+                            void *out, int coverage, int64_t row0, int64_t n_total,
+                            cudaStream_t s);
+// tensor-core split-BF16 Gram (gram_tc.cu)
+constexpr int kTcTileM = 128;    // rows of the I block per tile
+constexpr int kTcTileN = 256;    // rows of the J block per tile
+cudaError_t make_tc_tensor_maps(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
+                                int64_t n, int64_t Dp, void **tmap_hi, void **tmap_lo);
+cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
+                           const double *rs, const int32_t *tiles, int64_t n_tiles,
+                           int32_t *queue, int32_t *status, double *g64, void *out,
+                           int coverage, cudaStream_t s);
+// CTAs of one Gram launch and the FP64 scratch (doubles) it needs: one
+// 128 x 256 FP64 partial-sum tile per CTA
+int64_t tc_grid(int64_t n_tiles);
+size_t tc_scratch_doubles(int64_t n_tiles);
+void free_tc_tensor_maps(void *tmap_hi, void *tmap_lo);
+void tc_tiles(int64_t n, std::vector<int32_t> &tiles);   // (I-block of 128, J-block of 256)
+
+// clouds (overlap.cu)
+cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,
+                           int coverage, int32_t *queue, cudaStream_t s);
+// adjoint (params_io == NULL: grad_params = grad_out * grad f) or one fused
+// ascent step (params_io != NULL: params_io += eta grad f / f where f >= fmin)
+cudaError_t launch_overlap_grad_q(const CloudStore &cs, int32_t *queue, const float *params,
+                                  const float *grad_out, float *grad_params, float *f_out,
+                                  float eta, float fmin, float *params_io, int32_t *flags,
+                                  cudaStream_t s);
+constexpr int kOverlapMaxRowJobs = 128;   // chunks of one I block
+constexpr int kOverlapMaxBlockItems = 32;
+cudaError_t launch_cloud_pack(const float *x, const float *y, const float *z,
+                              const float *sigma, const float *w, const int64_t *src_off,
+                              const int32_t *perm, const int64_t *poff, int64_t n, int dim,
+                              float4 *pts, float *lw, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace ap

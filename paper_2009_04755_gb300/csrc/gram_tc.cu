@@ -1,0 +1,460 @@
+// gram_tc.cu -- split-BF16 Gram of centred vectors on the 5th-generation
+// tensor cores (tcgen05), the contraction inside the Pearson correlation
+// (normalised cross correlation, Sec. V-A):
+//
+//   G_ij ~= Hi_i . Hi_j + Hi_i . Lo_j + Lo_i . Hi_j      (FP32 accumulation)
+//   r_ij  = G_ij * rs_i * rs_j,  rs = 1 / sqrt(ss)        (FP64 epilogue)
+//
+// One persistent CTA per SM pops tiles (a block of 128 items I x a block of
+// 256 items J, upper triangle only, recursive quadrant order) from an atomic
+// queue.  Warp roles inside the CTA:
+//   warp 0      one thread issues TMA tile loads (hi/lo of both blocks, 32
+//               columns per stage, 64-byte swizzle) into a 4-stage ring;
+//   warp 1      allocates 256 TMEM columns; one thread issues the three
+//               tcgen05.mma products per 16 columns into the TMEM accumulator
+//               and commits each stage back to the producer;
+//   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, FP64
+//               scaling, packed upper-triangle stores.
+// Every wait is bounded (kWaitBudgetNs); when one runs out the CTA records a
+// device error code, drains its in-flight copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr int BM = kTcTileM;                 // 128 rows of the I block
+constexpr int BN = kTcTileN;                 // 256 rows of the J block
+constexpr int BK = 32;                       // bf16 columns per stage (64 bytes)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;         // 8 KB
+constexpr int B_BYTES = BN * BK * 2;         // 16 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
+constexpr int TMEM_COLS = 2 * BN;            // two 128 x 256 FP32 accumulators
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
+constexpr int NUM_THREADS = 32 * (2 + kEpiWarps);
+constexpr int kChunkStages = 2;              // one accumulation chain = 64 columns of D
+constexpr int kFlushChunks = 64;             // FP32 register sums -> FP64 every 4096 columns
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false when the budget ran out or another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          volatile int *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitBudgetNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 64-byte swizzle,
+// 8-row core-matrix groups 512 bytes apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused, K fits the atom)
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)4 << 61;                    // swizzle mode: 64 B
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Accumulate one 64-column chunk of D (two stages) per TMEM accumulator
+// (two accumulators, double-buffered), so the tensor core never carries a
+// long FP32 chain; eight epilogue warps drain each chunk into FP32 register
+// sums and fold those into FP64 scratch every kFlushChunks chunks.
+template <int COVER>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+               int64_t n, int64_t Dp, const double *__restrict__ rs,
+               const int32_t *__restrict__ tiles, int64_t n_tiles, int32_t *queue,
+               int32_t *status, double *__restrict__ g64, void *out) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int *s_tile = reinterpret_cast<int *>(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t smem_base = smem_u32(smem);
+  auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty_bar = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+  auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * STAGES + a]); };
+  auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * STAGES + 2 + a]); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), kEpiWarps);
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // pipeline state (each role keeps its own copy)
+  uint32_t p_stage = 0, p_phase = 0, m_stage = 0, m_phase = 0;
+  uint32_t cc = 0;                          // chunks consumed so far (accumulator ring)
+  uint32_t issued_parity[STAGES];
+  bool issued[STAGES];
+#pragma unroll
+  for (int s = 0; s < STAGES; ++s) { issued[s] = false; issued_parity[s] = 0; }
+  const int64_t nk = Dp / BK;
+  const int64_t nchunks = COVER ? 0 : nk / kChunkStages;
+  double *my_g64 = g64 + (size_t)blockIdx.x * (BN * BM);
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = atomicAdd(queue, 1);
+      if (*s_abort || *reinterpret_cast<volatile int32_t *>(status) != 0) t = (int)n_tiles;
+      *s_tile = t;
+    }
+    __syncthreads();
+    const int64_t t = *s_tile;
+    if (t >= n_tiles) break;
+    const int32_t i0 = tiles[2 * t] * BM;
+    const int32_t j0 = tiles[2 * t + 1] * BN;
+
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      for (int64_t kb = 0; kb < nchunks * kChunkStages; ++kb) {
+        if (!mbar_wait(empty_bar(p_stage), p_phase ^ 1, s_abort)) {
+          atomicCAS(status, 0, DEV_TIMEOUT_EMPTY);
+          *s_abort = 1;
+          break;
+        }
+        const uint32_t fb = full_bar(p_stage);
+        const uint32_t sb = smem_base + p_stage * STAGE_BYTES;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        const int32_t k = (int32_t)(kb * BK);
+        tma_load_2d(sb, &tm_hi, fb, k, i0);
+        tma_load_2d(sb + A_BYTES, &tm_lo, fb, k, i0);
+        tma_load_2d(sb + 2 * A_BYTES, &tm_hi, fb, k, j0);
+        tma_load_2d(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, j0 + BM);
+        tma_load_2d(sb + 2 * A_BYTES + B_BYTES, &tm_lo, fb, k, j0);
+        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, j0 + BM);
+        issued[p_stage] = true;
+        issued_parity[p_stage] = p_phase;
+        if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer ----------------
+      uint32_t mc = cc;
+      for (int64_t c = 0; c < nchunks && !*s_abort; ++c, ++mc) {
+        const uint32_t a = mc & 1, use = mc >> 1;
+        if (!mbar_wait(tempty_bar(a), (use & 1) ^ 1, s_abort)) {
+          atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
+          *s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + a * BN;
+        bool ok = true;
+        for (int s = 0; s < kChunkStages; ++s) {
+          if (!mbar_wait(full_bar(m_stage), m_phase, s_abort)) {
+            atomicCAS(status, 0, DEV_TIMEOUT_FULL);
+            *s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = smem_base + m_stage * STAGE_BYTES;
+          const uint32_t a_hi = sb, a_lo = sb + A_BYTES;
+          const uint32_t b_hi = sb + 2 * A_BYTES, b_lo = sb + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;    // 16 bf16 = 32 bytes inside the swizzle atom
+            const uint64_t dah = sw64_desc(a_hi + off), dal = sw64_desc(a_lo + off);
+            const uint64_t dbh = sw64_desc(b_hi + off), dbl = sw64_desc(b_lo + off);
+            umma_bf16(dt, dah, dbh, (s | kk) != 0 ? 1u : 0u);
+            umma_bf16(dt, dah, dbl, 1u);
+            umma_bf16(dt, dal, dbh, 1u);
+          }
+          umma_commit(empty_bar(m_stage));
+          if (++m_stage == STAGES) { m_stage = 0; m_phase ^= 1; }
+        }
+        if (!ok) break;
+        umma_commit(tfull_bar(a));          // fires when this chunk's MMAs have landed
+      }
+    } else if (warp >= 2) {
+      // ---------------- epilogue ----------------
+      const int q = warp & 3;                // TMEM lane quarter this warp may access
+      const int h = (warp - 2) >> 2;         // column half of the 256-wide tile
+      const int row = q * 32 + lane;
+      const int64_t i = (int64_t)i0 + row;
+      float sum[BN / 2];
+#pragma unroll
+      for (int c = 0; c < BN / 2; ++c) sum[c] = 0.f;
+      bool flushed = false, ok = true;
+      uint32_t ec = cc;
+      for (int64_t c = 0; c < nchunks; ++c, ++ec) {
+        const uint32_t a = ec & 1, use = ec >> 1;
+        if (!mbar_wait(tfull_bar(a), use & 1, s_abort)) {
+          if (lane == 0) atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
+          *s_abort = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * BN + h * (BN / 2);
+#pragma unroll
+        for (int m = 0; m < BN / 2 / 32; ++m) {
+          uint32_t v[32];
+          tmem_ld32(taddr + m * 32, v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) sum[m * 32 + e] += __uint_as_float(v[e]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty_bar(a)) : "memory");
+        if ((c + 1) % kFlushChunks == 0 && c + 1 < nchunks) {
+          // fold the FP32 partial sums into FP64 scratch ([col][row] layout)
+#pragma unroll
+          for (int e = 0; e < BN / 2; ++e) {
+            double *gp = my_g64 + (size_t)(h * (BN / 2) + e) * BM + row;
+            const double prev = flushed ? *gp : 0.0;
+            *gp = prev + (double)sum[e];
+            sum[e] = 0.f;
+          }
+          flushed = true;
+        }
+      }
+      ok = ok && !*s_abort;
+      if (ok && i < n) {
+        const double ri = COVER ? 0.0 : rs[i];
+        const int64_t jb = (int64_t)j0 + h * (BN / 2);
+        int64_t p = pair_index(i, jb > i ? jb : i + 1, n);
+#pragma unroll
+        for (int e = 0; e < BN / 2; ++e) {
+          const int64_t j = jb + e;
+          if (j > i && j < n) {
+            if (COVER) {
+              atomicAdd(reinterpret_cast<int32_t *>(out) + p, 1);
+            } else {
+              double g = (double)sum[e];
+              if (flushed) g += my_g64[(size_t)(h * (BN / 2) + e) * BM + row];
+              reinterpret_cast<double *>(out)[p] = g * ri * rs[j];
+            }
+            ++p;
+          }
+        }
+      }
+    }
+    cc += (uint32_t)nchunks;
+    __syncthreads();
+  }
+
+  // teardown: the producer drains copies still in flight after an abort
+  if (warp == 0 && lane == 0 && *s_abort) {
+    for (int s = 0; s < STAGES; ++s) {
+      if (!issued[s]) continue;
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(full_bar(s), issued_parity[s])) {
+        if (global_ns() - t0 > kWaitBudgetNs) break;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+cudaError_t encode_rows(const __nv_bfloat16 *base, int64_t n, int64_t Dp, CUtensorMap *m) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t make_tc_tensor_maps(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t n,
+                                int64_t Dp, void **tmap_hi, void **tmap_lo) {
+  CUtensorMap *a = new CUtensorMap, *b = new CUtensorMap;
+  cudaError_t e = encode_rows(hi, n, Dp, a);
+  if (e == cudaSuccess) e = encode_rows(lo, n, Dp, b);
+  if (e != cudaSuccess) {
+    delete a;
+    delete b;
+    return e;
+  }
+  *tmap_hi = a;
+  *tmap_lo = b;
+  return cudaSuccess;
+}
+
+int64_t tc_grid(int64_t n_tiles) {
+  int64_t g = num_sms();
+  return g < n_tiles ? g : (n_tiles > 0 ? n_tiles : 1);
+}
+
+size_t tc_scratch_doubles(int64_t n_tiles) { return (size_t)tc_grid(n_tiles) * BM * BN; }
+
+void free_tc_tensor_maps(void *a, void *b) {
+  delete reinterpret_cast<CUtensorMap *>(a);
+  delete reinterpret_cast<CUtensorMap *>(b);
+}
+
+cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
+                           const double *rs, const int32_t *tiles, int64_t n_tiles,
+                           int32_t *queue, int32_t *status, double *g64, void *out,
+                           int coverage, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+  static bool attr_done[2] = {false, false};
+  auto kern = coverage ? gram_tc_kernel<1> : gram_tc_kernel<0>;
+  if (!attr_done[coverage ? 1 : 0]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done[coverage ? 1 : 0] = true;
+  }
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  int64_t grid = tc_grid(n_tiles);
+  kern<<<(int)grid, NUM_THREADS, SMEM_BYTES, s>>>(
+      *reinterpret_cast<const CUtensorMap *>(tmap_hi),
+      *reinterpret_cast<const CUtensorMap *>(tmap_lo), n, Dp, rs, tiles, n_tiles, queue, status,
+      g64, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ap

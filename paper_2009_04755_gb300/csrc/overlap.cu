@@ -1,0 +1,494 @@
+// overlap.cu -- Gaussian overlap cost between weighted point clouds, the
+// cross term of the GMM L2 distance used by the microscopy application
+// (Sec. V-C), its adjoint with respect to a rigid 2-D transform, and batched
+// gradient ascent for pairwise registration.
+//
+//   f(i,j) = sum_a sum_b w_a w_b exp(-|x_a - (R x_b + t)|^2 / (2 (s_a^2 + s_b^2)))
+//
+// Storage (built by cloud_pack): items in planner order, padded to multiples
+// of 4 points, s2k = 2 ln2 sigma^2 and lw = log2 w, so each term is
+//   w_a * 2^(lw_b - d^2 / (s2k_a + s2k_b))
+// = one add, one MUFU reciprocal, one FMA and one MUFU ex2 after d^2.
+// With a transform the a-points are moved instead of the b-points:
+//   |x_a - (R x_b + t)| = |R^T (x_a - t) - x_b|,
+// so the inner loop is unchanged, and the adjoint follows from
+//   df/dt = 2 ln2 * R sum e r d',   df/dtheta = 2 ln2 * sum e r (x_b d'_y - y_b d'_x)
+// with d' = R^T (x_a - t) - x_b and r = 1 / (s2k_a + s2k_b).
+//
+// Schedule: one persistent CTA per SM slot pops tiles (I block, J block) of
+// the upper triangle of item blocks from an atomic queue (Sec. IV-B).  The J
+// block's points are staged into shared memory with one bulk asynchronous
+// copy; the CTA's warps take "row jobs" (a chunk of 32*R points of one item
+// of I, held in registers, R per lane) and sweep every item of J with
+// broadcast shared-memory reads; per (row job, j) partials are reduced over
+// the warp with shuffles, then over the chunks of an item in a fixed order.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRowJobs = kOverlapMaxRowJobs;
+constexpr int kMaxBlockItems = kOverlapMaxBlockItems;
+constexpr float kTwoLn2 = 1.3862943611198906f;
+
+enum Mode { FWD = 0, FWD_T = 1, GRAD = 2, COVER = 3 };
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct TileCtx {
+  int32_t i_begin, i_end, j_begin, j_end;
+  int32_t n_rj;          // row jobs in this tile
+  int32_t use_smem;      // J block staged in shared memory
+  int64_t j_pt0;         // first storage point of the J block
+};
+
+struct Params {
+  const float4 *pts;
+  const float *lw;
+  const int64_t *poff;
+  const int32_t *cnt;    // real (unpadded) points per stored item
+  const int32_t *perm;
+  const int32_t *bstart;
+  const int32_t *tiles;
+  int64_t n_tiles;
+  int64_t n_items;
+  int32_t *queue;
+  int32_t *status;
+  int32_t stage_cap;     // points that fit the shared staging buffer
+  // outputs / extra inputs
+  float *out;            // FWD: f[P]; COVER: int32 counts[P]
+  const float *params;   // [P][3] (theta, tx, ty) or NULL
+  const float *grad_out; // [P] or NULL
+  float *grad_params;    // [P][3]
+  float *f_out;          // [P] or NULL
+  float *params_io;      // ascent: params updated in place
+  int32_t *flags;        // ascent: skipped steps
+  float eta, fmin;
+};
+
+template <int DIM, bool HAS_W, int MODE, int R>
+__global__ void __launch_bounds__(kThreads)
+overlap_kernel(Params P) {
+  constexpr int NV = (MODE == GRAD) ? 4 : 1;     // partial values per (row job, j)
+  constexpr int CH = 32 * R;                     // points per chunk
+  extern __shared__ __align__(16) uint8_t smem[];
+  float4 *s_pts = reinterpret_cast<float4 *>(smem);
+  float *s_lw = reinterpret_cast<float *>(s_pts + P.stage_cap);
+  float *s_part = (DIM == 3 && HAS_W) ? s_lw + P.stage_cap : s_lw;
+  int16_t *s_rj_item = reinterpret_cast<int16_t *>(s_part + kMaxRowJobs * kMaxBlockItems * NV);
+  int16_t *s_rj_chunk = s_rj_item + kMaxRowJobs;
+  int16_t *s_rj_first = s_rj_chunk + kMaxRowJobs;            // [kMaxBlockItems + 1]
+  uint64_t *s_bar = reinterpret_cast<uint64_t *>(
+      (reinterpret_cast<uintptr_t>(s_rj_first + kMaxBlockItems + 1) + 7) & ~uintptr_t(7));
+  TileCtx *s_ctx = reinterpret_cast<TileCtx *>(s_bar + 1);
+  int *s_tile = reinterpret_cast<int *>(s_ctx + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar = smem_u32(s_bar);
+  uint32_t phase = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int t = atomicAdd(P.queue, 1);
+      if (*reinterpret_cast<volatile int32_t *>(P.status) != 0) t = (int)P.n_tiles;
+      *s_tile = t;
+      if (t < P.n_tiles) {
+        const int IB = P.tiles[2 * t], JB = P.tiles[2 * t + 1];
+        TileCtx c;
+        c.i_begin = P.bstart[IB]; c.i_end = P.bstart[IB + 1];
+        c.j_begin = P.bstart[JB]; c.j_end = P.bstart[JB + 1];
+        int nrj = 0;
+        for (int i = c.i_begin; i < c.i_end; ++i) {
+          s_rj_first[i - c.i_begin] = (int16_t)nrj;
+          const int64_t np = P.cnt[i];
+          const int nch = (int)((np + CH - 1) / CH);
+          for (int ch = 0; ch < nch && nrj < kMaxRowJobs; ++ch) {
+            s_rj_item[nrj] = (int16_t)(i - c.i_begin);
+            s_rj_chunk[nrj] = (int16_t)ch;
+            ++nrj;
+          }
+        }
+        s_rj_first[c.i_end - c.i_begin] = (int16_t)nrj;
+        c.n_rj = nrj;
+        c.j_pt0 = P.poff[c.j_begin];
+        const int64_t jpts = P.poff[c.j_end] - c.j_pt0;
+        c.use_smem = (MODE != COVER) && jpts > 0 && jpts <= P.stage_cap;
+        if (c.use_smem) {
+          // stage the J block: one bulk asynchronous copy per array
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          uint32_t bytes = (uint32_t)(jpts * 16);
+          if (DIM == 3 && HAS_W) bytes += (uint32_t)(jpts * 4);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                       "r"(bytes)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                  "r"(smem_u32(s_pts)),
+              "l"(P.pts + c.j_pt0), "r"((uint32_t)(jpts * 16)), "r"(bar)
+              : "memory");
+          if (DIM == 3 && HAS_W)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                    "r"(smem_u32(s_lw)),
+                "l"(P.lw + c.j_pt0), "r"((uint32_t)(jpts * 4)), "r"(bar)
+                : "memory");
+        }
+        *s_ctx = c;
+      }
+    }
+    __syncthreads();
+    const int t = *s_tile;
+    if (t >= P.n_tiles) break;
+    const TileCtx c = *s_ctx;
+    const int nJ = c.j_end - c.j_begin;
+    const bool diag = (P.tiles[2 * t] == P.tiles[2 * t + 1]);
+
+    if (c.use_smem) {
+      bool ok = true;
+      uint32_t done = 0;
+      const uint64_t t0 = global_ns();
+      for (uint32_t it = 0;; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) break;
+        if ((it & 255u) == 255u && global_ns() - t0 > kWaitBudgetNs) { ok = false; break; }
+      }
+      phase ^= 1;
+      if (!ok && threadIdx.x == 0) atomicCAS(P.status, 0, DEV_TIMEOUT_STAGE);
+    }
+
+    if (MODE != COVER) {
+      const float4 *bsrc = c.use_smem ? s_pts : (P.pts + c.j_pt0);
+      const float *lsrc = c.use_smem ? s_lw : (P.lw ? P.lw + c.j_pt0 : nullptr);
+      for (int rj = warp; rj < c.n_rj; rj += kWarps) {
+        const int il = s_rj_item[rj];
+        const int i = c.i_begin + il;
+        const int64_t a_begin = P.poff[i] + (int64_t)s_rj_chunk[rj] * CH;
+        const int64_t a_end = P.poff[i] + P.cnt[i];
+        // this lane's a-points (padding and out-of-chunk points get weight 0)
+        float ax[R], ay[R], az[R], as[R], aw[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int64_t a = a_begin + r * 32 + lane;
+          if (a < a_end) {
+            float4 p = __ldg(P.pts + a);
+            ax[r] = p.x; ay[r] = p.y;
+            if (DIM == 3) { az[r] = p.z; as[r] = p.w; aw[r] = HAS_W ? exp2f(__ldg(P.lw + a)) : 1.f; }
+            else { az[r] = 0.f; as[r] = p.z; aw[r] = exp2f(p.w); }
+          } else {
+            ax[r] = 0.f; ay[r] = 0.f; az[r] = 0.f; as[r] = 1.f; aw[r] = 0.f;
+          }
+        }
+        const int j_first = diag ? (il + 1) : 0;
+        for (int jl = j_first; jl < nJ; ++jl) {
+          const int j = c.j_begin + jl;
+          const int b0 = (int)(P.poff[j] - c.j_pt0), b1 = b0 + P.cnt[j];
+          // transformed a-points for this pair: a' = R^T (x_a - t)
+          float tx_[R], ty_[R];
+          float cth = 1.f, sth = 0.f, ttx = 0.f, tty = 0.f;
+          int64_t pidx = 0;
+          if (MODE == FWD_T || MODE == GRAD) {
+            const int oi = P.perm[i], oj = P.perm[j];
+            pidx = pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
+            const float *pp = (MODE == GRAD && P.params_io) ? P.params_io : P.params;
+            if (pp) {
+              const float th = pp[3 * pidx];
+              ttx = pp[3 * pidx + 1]; tty = pp[3 * pidx + 2];
+              sincosf(th, &sth, &cth);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (MODE == FWD_T || MODE == GRAD) {
+              const float ux = ax[r] - ttx, uy = ay[r] - tty;
+              tx_[r] = cth * ux + sth * uy;
+              ty_[r] = -sth * ux + cth * uy;
+            } else {
+              tx_[r] = ax[r]; ty_[r] = ay[r];
+            }
+          }
+          float accF[R], cmpF[R], accX[R], accY[R], accT[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) { accF[r] = 0.f; cmpF[r] = 0.f; accX[r] = 0.f; accY[r] = 0.f; accT[r] = 0.f; }
+          for (int bb0 = b0; bb0 < b1; bb0 += 32) {
+            const int bb1 = min(bb0 + 32, b1);
+            float blF[R], blX[R], blY[R], blT[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { blF[r] = 0.f; blX[r] = 0.f; blY[r] = 0.f; blT[r] = 0.f; }
+#pragma unroll 4
+            for (int b = bb0; b < bb1; ++b) {
+              const float4 q = bsrc[b];
+              float lwb, s2b;
+              if (DIM == 3) { s2b = q.w; lwb = HAS_W ? lsrc[b] : 0.f; }
+              else { s2b = q.z; lwb = q.w; }
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                const float dx = tx_[r] - q.x, dy = ty_[r] - q.y;
+                float d2 = dx * dx;
+                d2 = fmaf(dy, dy, d2);
+                if (DIM == 3) { const float dz = az[r] - q.z; d2 = fmaf(dz, dz, d2); }
+                const float rr = rcp_approx(as[r] + s2b);
+                const float e = ex2_approx(fmaf(-d2, rr, lwb));
+                blF[r] += e;
+                if (MODE == GRAD) {
+                  const float er = e * rr;
+                  blX[r] = fmaf(er, dx, blX[r]);
+                  blY[r] = fmaf(er, dy, blY[r]);
+                  blT[r] = fmaf(er, fmaf(q.x, dy, -q.y * dx), blT[r]);
+                }
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              // compensated add of the block sum
+              const float yk = blF[r] - cmpF[r];
+              const float tk = accF[r] + yk;
+              cmpF[r] = (tk - accF[r]) - yk;
+              accF[r] = tk;
+              if (MODE == GRAD) { accX[r] += blX[r]; accY[r] += blY[r]; accT[r] += blT[r]; }
+            }
+          }
+          float vF = 0.f, vX = 0.f, vY = 0.f, vT = 0.f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            vF = fmaf(aw[r], accF[r], vF);
+            if (MODE == GRAD) {
+              vX = fmaf(aw[r], accX[r], vX);
+              vY = fmaf(aw[r], accY[r], vY);
+              vT = fmaf(aw[r], accT[r], vT);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            vF += __shfl_xor_sync(0xffffffffu, vF, o);
+            if (MODE == GRAD) {
+              vX += __shfl_xor_sync(0xffffffffu, vX, o);
+              vY += __shfl_xor_sync(0xffffffffu, vY, o);
+              vT += __shfl_xor_sync(0xffffffffu, vT, o);
+            }
+          }
+          if (lane == 0) {
+            float *dst = s_part + ((size_t)rj * kMaxBlockItems + jl) * NV;
+            dst[0] = vF;
+            if (MODE == GRAD) { dst[1] = vX; dst[2] = vY; dst[3] = vT; }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // fixed-order reduction over the chunks of each item, then the stores
+    const int nI = c.i_end - c.i_begin;
+    for (int q = threadIdx.x; q < nI * nJ; q += kThreads) {
+      const int il = q / nJ, jl = q - il * nJ;
+      if (diag && jl <= il) continue;
+      const int i = c.i_begin + il, j = c.j_begin + jl;
+      const int oi = P.perm[i], oj = P.perm[j];
+      const int64_t p = pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
+      if (MODE == COVER) {
+        atomicAdd(reinterpret_cast<int32_t *>(P.out) + p, 1);
+        continue;
+      }
+      double sF = 0.0, sX = 0.0, sY = 0.0, sT = 0.0;
+      for (int rj = s_rj_first[il]; rj < s_rj_first[il + 1]; ++rj) {
+        const float *src = s_part + ((size_t)rj * kMaxBlockItems + jl) * NV;
+        sF += (double)src[0];
+        if (MODE == GRAD) { sX += (double)src[1]; sY += (double)src[2]; sT += (double)src[3]; }
+      }
+      if (MODE == FWD || MODE == FWD_T) {
+        P.out[p] = (float)sF;
+      } else if (MODE == GRAD) {
+        // rotate the translation part back: df/dt = 2 ln2 R sum e r d'
+        const float *pp = P.params_io ? P.params_io : P.params;
+        float th = 0.f, ttx = 0.f, tty = 0.f;
+        if (pp) { th = pp[3 * p]; ttx = pp[3 * p + 1]; tty = pp[3 * p + 2]; }
+        float sth, cth;
+        sincosf(th, &sth, &cth);
+        const float f = (float)sF;
+        const float gx = kTwoLn2 * (float)(cth * sX - sth * sY);
+        const float gy = kTwoLn2 * (float)(sth * sX + cth * sY);
+        const float gt = kTwoLn2 * (float)sT;
+        if (P.f_out) P.f_out[p] = f;
+        if (P.params_io) {
+          // one ascent step on log f
+          if (f >= P.fmin) {
+            const float s = P.eta / f;
+            P.params_io[3 * p] = th + s * gt;
+            P.params_io[3 * p + 1] = ttx + s * gx;
+            P.params_io[3 * p + 2] = tty + s * gy;
+          } else if (P.flags) {
+            P.flags[p] = 1;
+          }
+        } else {
+          const float go = P.grad_out ? P.grad_out[p] : 1.f;
+          P.grad_params[3 * p] = go * gt;
+          P.grad_params[3 * p + 1] = go * gx;
+          P.grad_params[3 * p + 2] = go * gy;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pack one item per CTA into planner order, padded to a multiple of 4 points.
+__global__ void cloud_pack_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                  const float *__restrict__ z, const float *__restrict__ sigma,
+                                  const float *__restrict__ w, const int64_t *__restrict__ src_off,
+                                  const int32_t *__restrict__ perm,
+                                  const int64_t *__restrict__ poff, int64_t n, int dim,
+                                  float4 *__restrict__ pts, float *__restrict__ lw) {
+  const double two_ln2 = 1.3862943611198906;
+  for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    const int64_t o = perm[s];
+    const int64_t src0 = src_off[o], cnt = src_off[o + 1] - src_off[o];
+    const int64_t dst0 = poff[s], pcnt = poff[s + 1] - poff[s];
+    for (int64_t k = threadIdx.x; k < pcnt; k += blockDim.x) {
+      float4 p;
+      float l;
+      if (k < cnt) {
+        const int64_t a = src0 + k;
+        const double sg = (double)sigma[a];
+        const float s2k = (float)(two_ln2 * sg * sg);
+        const float wt = w ? w[a] : 1.f;
+        l = (wt > 0.f) ? (float)log2((double)wt) : -INFINITY;
+        if (dim == 3) p = make_float4(x[a], y[a], z[a], s2k);
+        else p = make_float4(x[a], y[a], s2k, l);
+      } else {
+        // padding (never visited: loops use the real counts), kept finite
+        l = -INFINITY;
+        if (dim == 3) p = make_float4(0.f, 0.f, 0.f, 1.f);
+        else p = make_float4(0.f, 0.f, 1.f, -INFINITY);
+      }
+      pts[dst0 + k] = p;
+      if (lw) lw[dst0 + k] = l;
+    }
+  }
+}
+
+template <int DIM, bool HAS_W, int MODE>
+cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s) {
+  constexpr int NV = (MODE == GRAD) ? 4 : 1;
+  size_t smem = (size_t)P.stage_cap * 16 + ((DIM == 3 && HAS_W) ? (size_t)P.stage_cap * 4 : 0) +
+                (size_t)kMaxRowJobs * kMaxBlockItems * NV * 4 +
+                (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
+  void (*kern)(Params) = nullptr;
+  switch (reg_r) {
+    case 1: kern = overlap_kernel<DIM, HAS_W, MODE, 1>; break;
+    case 2: kern = overlap_kernel<DIM, HAS_W, MODE, 2>; break;
+    default: kern = overlap_kernel<DIM, HAS_W, MODE, 4>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > P.n_tiles) grid = P.n_tiles;
+  e = cudaMemsetAsync(P.queue, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  kern<<<(int)grid, kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+Params base_params(const CloudStore &cs, int32_t *queue, int32_t *status) {
+  Params P{};
+  P.pts = cs.d_pts;
+  P.lw = cs.d_lw;
+  P.poff = cs.d_poff;
+  P.cnt = cs.d_cnt;
+  P.perm = cs.d_perm;
+  P.bstart = cs.d_bstart;
+  P.tiles = cs.d_tiles;
+  P.n_tiles = cs.n_tiles;
+  P.n_items = cs.n;
+  P.queue = queue;
+  P.status = status;
+  P.stage_cap = cs.block_pts;
+  return P;
+}
+
+}  // namespace
+
+// status word lives right after the queue counter (see api.cu)
+static inline int32_t *status_of(int32_t *queue) { return queue + 1; }
+
+cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out, int coverage,
+                           int32_t *queue, cudaStream_t s) {
+  if (cs.n_tiles <= 0) return cudaSuccess;
+  Params P = base_params(cs, queue, status_of(queue));
+  P.out = out;
+  P.params = params;
+  const bool w3 = (cs.dim == 3) && !cs.unit_weights;
+  if (coverage) {
+    if (cs.dim == 3) return w3 ? launch_r<3, true, COVER>(cs, P, cs.reg_r, s) : launch_r<3, false, COVER>(cs, P, cs.reg_r, s);
+    return launch_r<2, true, COVER>(cs, P, cs.reg_r, s);
+  }
+  if (params) return launch_r<2, true, FWD_T>(cs, P, cs.reg_r, s);
+  if (cs.dim == 3) return w3 ? launch_r<3, true, FWD>(cs, P, cs.reg_r, s) : launch_r<3, false, FWD>(cs, P, cs.reg_r, s);
+  return launch_r<2, true, FWD>(cs, P, cs.reg_r, s);
+}
+
+cudaError_t launch_overlap_grad_q(const CloudStore &cs, int32_t *queue, const float *params,
+                                  const float *grad_out, float *grad_params, float *f_out,
+                                  float eta, float fmin, float *params_io, int32_t *flags,
+                                  cudaStream_t s) {
+  if (cs.n_tiles <= 0) return cudaSuccess;
+  Params P = base_params(cs, queue, status_of(queue));
+  P.params = params;
+  P.grad_out = grad_out;
+  P.grad_params = grad_params;
+  P.f_out = f_out;
+  P.params_io = params_io;
+  P.flags = flags;
+  P.eta = eta;
+  P.fmin = fmin;
+  return launch_r<2, true, GRAD>(cs, P, cs.reg_r, s);
+}
+
+cudaError_t launch_cloud_pack(const float *x, const float *y, const float *z, const float *sigma,
+                              const float *w, const int64_t *src_off, const int32_t *perm,
+                              const int64_t *poff, int64_t n, int dim, float4 *pts, float *lw,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)(n < 65535 ? n : 65535);
+  cloud_pack_kernel<<<grid, 128, 0, s>>>(x, y, z, sigma, w, src_off, perm, poff, n, dim, pts, lw);
+  return cudaGetLastError();
+}
+
+}  // namespace ap

@@ -1,0 +1,73 @@
+"""Shared helpers of the GPU parity tests (tolerances written out here)."""
+import numpy as np
+
+# FP32 overlap: 1e-5 relative on pairs whose FP32 evaluation is well
+# conditioned (kappa * 2^-23 * 8 <= 1e-5, f >= 1e-30); every other pair must
+# stay within a few times the oracle's FP32 error scale sum (|arg|+4) 2^-23 e.
+OVERLAP_RTOL = 1e-5
+OVERLAP_BOUND_FACTOR = 3.0
+# split-BF16 and FP32 Pearson: absolute error per correlation at the workload
+# sizes (long vectors)
+PEARSON_ATOL = 1e-6
+
+
+def pearson_tolerance(X, pi, pj, prec):
+    """Per-pair error allowance of the GPU paths for short vectors.
+
+    split-BF16: c = hi + lo + d with |d| <= 2^-16 |c| (two round-to-nearest
+    steps at unit roundoff 2^-8), and the dropped lo*lo term is <= 2^-16
+    |c_i c_j|, so each product is off by at most 3 * 2^-16 |c_i c_j|; with
+    independent signs the sum's error stays within 6 * 2^-16 *
+    sqrt(sum_k c_ik^2 c_jk^2), divided by sqrt(ss_i ss_j).  It falls like
+    1/sqrt(D) and is far below 1e-6 at D = 2^20.
+    FP32: round-to-nearest accumulation over D terms, a random walk of
+    relative size ~2^-24 sqrt(D); allowance 2^-22 sqrt(D) |r|.
+    """
+    X = np.asarray(X, np.float64)
+    C = X - X.mean(1, keepdims=True)
+    ss = (C * C).sum(1)
+    D = X.shape[1]
+    if prec == 1:
+        S2 = C * C
+        num = np.sqrt(np.einsum("pk,pk->p", S2[pi], S2[pj]))
+        return PEARSON_ATOL + 6 * 2.0 ** -16 * num / np.sqrt(ss[pi] * ss[pj])
+    r = np.einsum("pk,pk->p", C[pi], C[pj]) / np.sqrt(ss[pi] * ss[pj])
+    return PEARSON_ATOL + 2.0 ** -22 * np.sqrt(D) * np.abs(r)
+# adjoint: norm-wise, |g - g_ref|_inf <= 1e-4 max(|g_ref|_inf, 1e-6 sum w w)
+GRAD_RTOL = 1e-4
+
+
+def check_overlap(f_gpu, f_ref, kappa, bound, what=""):
+    f_gpu = np.asarray(f_gpu, np.float64)
+    err = np.abs(f_gpu - f_ref)
+    good = (kappa * 2.0 ** -23 * 8 <= 1e-5) & (f_ref >= 1e-30)
+    rel = err[good] / np.abs(f_ref[good])
+    assert good.mean() > 0.5, f"{what}: too few well-conditioned pairs ({good.mean():.3f})"
+    assert rel.max(initial=0.0) <= OVERLAP_RTOL, \
+        f"{what}: max rel err {rel.max():.3e} at {np.argmax(rel)}"
+    bad = ~good
+    if bad.any():
+        lim = np.maximum(OVERLAP_BOUND_FACTOR * bound[bad], OVERLAP_RTOL * np.abs(f_ref[bad]))
+        over = err[bad] > lim + 1e-37
+        assert not over.any(), f"{what}: {over.sum()} ill-conditioned pairs beyond bound"
+    return float(rel.max(initial=0.0))
+
+
+def check_grad(g_gpu, g_ref, wsum):
+    g_gpu = np.asarray(g_gpu, np.float64)
+    scale = np.maximum(np.abs(g_ref).max(1), 1e-6 * wsum)
+    err = np.abs(g_gpu - g_ref).max(1)
+    worst = float((err / scale).max())
+    assert worst <= GRAD_RTOL, f"grad norm-wise rel err {worst:.3e}"
+    return worst
+
+
+def cloud_wsum(c, pi, pj):
+    off = c["offsets"]
+    w = c.get("weight")
+    if w is None:
+        sz = np.diff(off)
+        return sz[pi] * sz[pj]
+    cs = np.concatenate([[0.0], np.cumsum(np.asarray(w, np.float64))])
+    ws = cs[off[1:]] - cs[off[:-1]]
+    return ws[pi] * ws[pj]

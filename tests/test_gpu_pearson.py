@@ -1,0 +1,170 @@
+"""GPU parity of the Pearson path (split-BF16 tcgen05 Gram and plain FP32
+Gram, FP64 normalisation) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import PEARSON_ATOL, pearson_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ap():
+    import paper_2009_04755_gb300 as ap
+    ap.lib()
+    return ap
+
+
+def _run(ap, X, prec, precisions=None, host=False):
+    precisions = precisions or (prec,)
+    src = X.pin_memory() if host else X.cuda()
+    with ap.Items.from_vectors(src, precisions=precisions) as it:
+        out = it.run_pairs(ap.AP_FN_PEARSON, prec).cpu().numpy()
+        assert it.last_device_error() == 0
+    return out
+
+
+@pytest.mark.parametrize("n,D", [(300, 1000), (257, 64), (129, 2050), (2, 2), (40, 20000)])
+def test_pearson_all_pairs_match_oracle(ap, oracle_lib, n, D):
+    X = synth.vectors_grouped(n, D, seed=n + D)
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    both = (ap.AP_PREC_SPLIT_BF16, ap.AP_PREC_FP32)
+    for prec in both:
+        got = _run(ap, X, prec, precisions=both)
+        tol = pearson_tolerance(X.numpy(), pi, pj, prec)
+        over = np.abs(got - ref) > tol
+        assert not over.any(), f"prec {prec}: {over.sum()} pairs beyond tolerance, " \
+            f"max |err| {np.abs(got - ref).max():.3e}"
+        if D >= 16384:
+            assert np.abs(got - ref).max() <= PEARSON_ATOL
+
+
+@pytest.mark.parametrize("D", [4096, 1 << 16])
+def test_pearson_strongly_correlated(ap, oracle_lib, D):
+    # long correlated chains: the accumulation must not drift (a single FP32
+    # tensor-core chain over D would be biased by ~2^-23 D/64 relative)
+    n = 64
+    g = torch.Generator().manual_seed(3)
+    base = torch.randn(1, D, generator=g)
+    X = (base + 0.1 * torch.randn(n, D, generator=g)).float()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    got = _run(ap, X, ap.AP_PREC_SPLIT_BF16)
+    assert ref.min() > 0.98
+    assert np.all(np.abs(got - ref) <= pearson_tolerance(X.numpy(), pi, pj, 1))
+    if D >= 16384:
+        assert np.abs(got - ref).max() <= PEARSON_ATOL
+
+
+def test_pearson_host_source_equals_device_source(ap):
+    n, D = 200, 3000
+    X = synth.vectors_grouped(n, D, seed=9)
+    a = _run(ap, X, ap.AP_PREC_SPLIT_BF16, host=False)
+    b = _run(ap, X, ap.AP_PREC_SPLIT_BF16, host=True)
+    assert np.array_equal(a, b)
+
+
+def test_pearson_update_items_reuses_storage(ap, oracle_lib):
+    n, D = 150, 512
+    X1 = synth.vectors_grouped(n, D, seed=1)
+    X2 = synth.vectors_grouped(n, D, seed=2)
+    pi, pj = oracle_lib.all_pairs(n)
+    with ap.Items.from_vectors(X1.cuda()) as it:
+        it.update(X2.cuda())
+        got = it.run_pairs().cpu().numpy()
+    ref = oracle_lib.pearson(X2.numpy(), pi, pj)
+    assert np.all(np.abs(got - ref) <= pearson_tolerance(X2.numpy(), pi, pj, 1))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_pearson_coverage_every_pair_once(ap, prec, oracle_lib):
+    n, D = 777, 64
+    X = synth.vectors_grouped(n, D, seed=4)
+    with ap.Items.from_vectors(X.cuda(), precisions=(prec,)) as it:
+        cnt = it.run_pairs(ap.AP_FN_COVERAGE, prec).cpu().numpy()
+    assert cnt.shape == (oracle_lib.pair_count(n),)
+    assert np.all(cnt == 1)
+
+
+def test_pearson_edge_cases(ap):
+    # n < 2: nothing to do
+    for n in (0, 1):
+        X = torch.randn(max(n, 1), 16)[:n].contiguous()
+        with ap.Items.from_vectors(X.cuda()) as it:
+            assert it.run_pairs().numel() == 0
+    # zero-variance item gives NaN for its pairs only
+    X = torch.randn(5, 100)
+    X[2] = 3.0
+    with ap.Items.from_vectors(X.cuda()) as it:
+        r = it.run_pairs().cpu().numpy()
+    bad = [ap.pair_index(i, 2, 5) for i in range(2)] + [ap.pair_index(2, j, 5) for j in (3, 4)]
+    assert np.all(np.isnan(r[bad]))
+    good = np.setdiff1d(np.arange(10), bad)
+    assert np.all(np.isfinite(r[good]))
+
+
+def test_pearson_rejects_bad_requests(ap):
+    X = torch.randn(10, 64)
+    with ap.Items.from_vectors(X.cuda(), precisions=(ap.AP_PREC_SPLIT_BF16,)) as it:
+        with pytest.raises(ap.APError) as e:
+            it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32)   # representation not built
+        assert e.value.status == 6
+        with pytest.raises(ap.APError) as e:
+            it.run_pairs(ap.AP_FN_OVERLAP)
+        assert e.value.status == 1
+
+
+def _sample_pairs(n, rng, n_random=1500):
+    i, j = [], []
+    # all pairs of two random 128 x 256 tiles and one diagonal tile
+    for _ in range(2):
+        a0 = int(rng.integers(0, n // 128)) * 128
+        b0 = int(rng.integers(a0 // 256, n // 256)) * 256
+        for a in range(a0, a0 + 128, 9):
+            for b in range(b0, b0 + 256, 17):
+                if a < b:
+                    i.append(a); j.append(b)
+    d0 = int(rng.integers(0, n // 256)) * 256
+    for a in range(d0, d0 + 256, 11):
+        for b in range(a + 1, d0 + 256, 13):
+            i.append(a); j.append(b)
+    # first row, the last two rows
+    for b in range(1, n, 97):
+        i.append(0); j.append(b)
+    i.append(n - 2); j.append(n - 1)
+    a = rng.integers(0, n - 1, n_random)
+    b = rng.integers(0, n, n_random)
+    keep = a < b
+    i.extend(a[keep].tolist()); j.extend(b[keep].tolist())
+    return np.array(i, np.int64), np.array(j, np.int64)
+
+
+def test_pearson_full_size_sampled(ap, oracle_lib):
+    """The benchmark's workload (8192 vectors of 2^20 FP32, groups of 16) in
+    the benchmark's launch configuration, checked on sampled pairs."""
+    n, D = 8192, 1 << 20
+    X = synth.vectors_grouped(n, D, seed=0, device="cuda")
+    both = (ap.AP_PREC_SPLIT_BF16, ap.AP_PREC_FP32)
+    with ap.Items.from_vectors(X, precisions=both) as it:
+        r_tc = it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_SPLIT_BF16)
+        r_32 = it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32)
+        torch.cuda.synchronize()
+        assert it.last_device_error() == 0
+        rng = np.random.default_rng(0)
+        pi, pj = _sample_pairs(n, rng)
+        rows = np.unique(np.concatenate([pi, pj]))
+        sub = X[torch.from_numpy(rows).cuda()].cpu().numpy()
+        remap = {r: k for k, r in enumerate(rows)}
+        ref = oracle_lib.pearson(sub, [remap[a] for a in pi], [remap[b] for b in pj])
+        p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+        got_tc = r_tc[p].cpu().numpy()
+        got_32 = r_32[p].cpu().numpy()
+        assert np.abs(got_tc - ref).max() <= PEARSON_ATOL
+        assert np.abs(got_32 - ref).max() <= PEARSON_ATOL
+        assert torch.isfinite(r_tc).all() and torch.isfinite(r_32).all()
+        # every correlation is a correlation
+        assert float(r_tc.abs().max()) <= 1.0
