@@ -75,6 +75,8 @@ struct VecStore {
   int64_t Dp = 0;                   // padded row length (multiple of 64)
   uint32_t precisions = 0;
   double *d_mu = nullptr, *d_ss = nullptr, *d_rs = nullptr;   // FP64 per item
+  double *d_part = nullptr;         // [n][kSplitParts] partial sums of c^2
+  int64_t n_rows_alloc = 0;         // rows rounded up to the row block
   __nv_bfloat16 *d_hi = nullptr, *d_lo = nullptr;              // [n][Dp]
   float *d_c32 = nullptr;                                      // [n][Dp]
   float *d_stage = nullptr;         // raw rows staged from the host
@@ -126,11 +128,24 @@ void make_blocks(const std::vector<int64_t> &poff, const std::vector<int64_t> &c
 // kernel launchers
 // ---------------------------------------------------------------------------
 // vectors (vec.cu)
-cudaError_t launch_vec_stats(const float *X, int64_t n, int64_t D, int64_t ld,
-                             double *mu, double *ss, double *rs, cudaStream_t s);
-cudaError_t launch_vec_split(const float *X, int64_t n, int64_t D, int64_t ld, int64_t Dp,
-                             const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                             float *c32, cudaStream_t s);
+// Blocked layout of the pre-processed copies: rows in blocks of 128 items,
+// columns in blocks of kblk; one (row block, column block) tile is a
+// contiguous 128 x kblk array, so every tile load is one contiguous run.
+constexpr int kRowBlock = 128;
+constexpr int kTcKBlock = 32;     // bf16 columns per block (64 bytes per row)
+constexpr int kF32KBlock = 16;    // fp32 columns per block (64 bytes per row)
+constexpr int kSplitParts = 64;   // FP64 partials of sum c^2 per row
+__host__ __device__ __forceinline__ size_t blocked_offset(int64_t row, int64_t k, int64_t nkb,
+                                                          int kblk) {
+  return ((size_t)(row / kRowBlock) * nkb + (size_t)(k / kblk)) * ((size_t)kRowBlock * kblk) +
+         (size_t)(row % kRowBlock) * kblk + (size_t)(k % kblk);
+}
+cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, double *mu,
+                            cudaStream_t s);
+// rows [row0, row0 + n) of the item set, X pointing at row row0
+cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t n, int64_t D, int64_t ld,
+                             int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                             float *c32, double *part, double *ss, double *rs, cudaStream_t s);
 cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
                             const int32_t *tiles, int64_t n_tiles, int32_t *queue,
                             void *out, int coverage, int64_t row0, int64_t n_total,

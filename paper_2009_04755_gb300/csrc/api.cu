@@ -66,7 +66,7 @@ void free_items(ap_items *it) {
   dfree(c.d_pts); dfree(c.d_lw); dfree(c.d_poff); dfree(c.d_cnt); dfree(c.d_perm);
   dfree(c.d_bstart); dfree(c.d_tiles);
   VecStore &v = it->vec;
-  dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
+  dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
   free_tc_tensor_maps(v.tmap_hi, v.tmap_lo);
   v.tmap_hi = v.tmap_lo = nullptr;
@@ -218,9 +218,10 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
   const bool split = (v.precisions & (1u << AP_PREC_SPLIT_BF16)) != 0;
   const bool f32 = (v.precisions & (1u << AP_PREC_FP32)) != 0;
   if (!on_host) {
-    AP_TRY(launch_vec_stats(data, v.n, v.D, v.ld, v.d_mu, v.d_ss, v.d_rs, s));
-    AP_TRY(launch_vec_split(data, v.n, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
-                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, s));
+    AP_TRY(launch_vec_mean(data, v.n, v.D, v.ld, v.d_mu, s));
+    AP_TRY(launch_vec_split(data, 0, v.n, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
+                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
+                            v.d_rs, s));
     return AP_OK;
   }
   // host source: two staging buffers, copies on the copy stream overlap the
@@ -246,13 +247,11 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
                           it->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(copied[b], it->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[b], 0);
+    if (e == cudaSuccess) e = launch_vec_mean(stage, nr, v.D, v.ld, v.d_mu + r0, s);
     if (e == cudaSuccess)
-      e = launch_vec_stats(stage, nr, v.D, v.ld, v.d_mu + r0, v.d_ss + r0, v.d_rs + r0, s);
-    if (e == cudaSuccess)
-      e = launch_vec_split(stage, nr, v.D, v.ld, v.Dp, v.d_mu + r0,
-                           split ? v.d_hi + r0 * v.Dp : nullptr,
-                           split ? v.d_lo + r0 * v.Dp : nullptr,
-                           f32 ? v.d_c32 + r0 * v.Dp : nullptr, s);
+      e = launch_vec_split(stage, r0, nr, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
+                           split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
+                           v.d_rs, s);
     if (e == cudaSuccess) e = cudaEventRecord(done[b], s);
   }
   if (e != cudaSuccess) st = from_cuda(e);
@@ -281,9 +280,15 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   AP_TRY(dmalloc(&v.d_mu, nn));
   AP_TRY(dmalloc(&v.d_ss, nn));
   AP_TRY(dmalloc(&v.d_rs, nn));
+  AP_TRY(dmalloc(&v.d_part, (size_t)nn * kSplitParts));
+  // blocked copies cover whole row blocks; the padding rows stay zero
+  v.n_rows_alloc = round_up(nn, kRowBlock);
+  const size_t elems = (size_t)v.n_rows_alloc * v.Dp;
   if (v.precisions & (1u << AP_PREC_SPLIT_BF16)) {
-    AP_TRY(dmalloc(&v.d_hi, (size_t)nn * v.Dp));
-    AP_TRY(dmalloc(&v.d_lo, (size_t)nn * v.Dp));
+    AP_TRY(dmalloc(&v.d_hi, elems));
+    AP_TRY(dmalloc(&v.d_lo, elems));
+    AP_TRY(cudaMemsetAsync(v.d_hi, 0, elems * 2, s));
+    AP_TRY(cudaMemsetAsync(v.d_lo, 0, elems * 2, s));
     AP_TRY(make_tc_tensor_maps(v.d_hi, v.d_lo, nn, v.Dp, &v.tmap_hi, &v.tmap_lo));
     std::vector<int32_t> tiles;
     tc_tiles(v.n, tiles);
@@ -294,7 +299,8 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
       AP_TRY(cudaMemcpy(v.d_tiles_tc, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
   }
   if (v.precisions & (1u << AP_PREC_FP32)) {
-    AP_TRY(dmalloc(&v.d_c32, (size_t)nn * v.Dp));
+    AP_TRY(dmalloc(&v.d_c32, elems));
+    AP_TRY(cudaMemsetAsync(v.d_c32, 0, elems * 4, s));
     std::vector<int32_t> tiles;
     dc_block_pairs((v.n + 127) / 128, tiles);
     v.n_tiles_f32 = (int64_t)tiles.size() / 2;

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int BM = kTcTileM;                 // 128 rows of the I block
 constexpr int BN = kTcTileN;                 // 256 rows of the J block
-constexpr int BK = 32;                       // bf16 columns per stage (64 bytes)
+constexpr int BK = kTcKBlock;                // bf16 columns per stage (64 bytes)
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;         // 8 KB
 constexpr int B_BYTES = BN * BK * 2;         // 16 KB
@@ -39,7 +39,7 @@ constexpr int TMEM_COLS = 2 * BN;            // two 128 x 256 FP32 accumulators
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int NUM_THREADS = 32 * (2 + kEpiWarps);
 constexpr int kChunkStages = 2;              // one accumulation chain = 64 columns of D
-constexpr int kFlushChunks = 64;             // FP32 register sums -> FP64 every 4096 columns
+constexpr int kFlushChunks = 256;            // FP32 register sums -> FP64 every 16384 columns
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
@@ -92,12 +92,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int32_t x, int32_t y) {
+// one 128-row x 32-column block of the blocked copy: coordinates
+// {column in block, row in block, column block, row block}
+__device__ __forceinline__ void tma_load_block(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                               int32_t kb, int32_t rb) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(0), "r"(kb), "r"(rb)
       : "memory");
 }
 
@@ -224,6 +226,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     if (t >= n_tiles) break;
     const int32_t i0 = tiles[2 * t] * BM;
     const int32_t j0 = tiles[2 * t + 1] * BN;
+    const int32_t rb_a = tiles[2 * t], rb_b = tiles[2 * t + 1] * (BN / BM);
 
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
@@ -236,13 +239,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         const uint32_t fb = full_bar(p_stage);
         const uint32_t sb = smem_base + p_stage * STAGE_BYTES;
         mbar_expect_tx(fb, STAGE_BYTES);
-        const int32_t k = (int32_t)(kb * BK);
-        tma_load_2d(sb, &tm_hi, fb, k, i0);
-        tma_load_2d(sb + A_BYTES, &tm_lo, fb, k, i0);
-        tma_load_2d(sb + 2 * A_BYTES, &tm_hi, fb, k, j0);
-        tma_load_2d(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, j0 + BM);
-        tma_load_2d(sb + 2 * A_BYTES + B_BYTES, &tm_lo, fb, k, j0);
-        tma_load_2d(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, j0 + BM);
+        const int32_t k = (int32_t)kb;
+        tma_load_block(sb, &tm_hi, fb, k, rb_a);
+        tma_load_block(sb + A_BYTES, &tm_lo, fb, k, rb_a);
+        tma_load_block(sb + 2 * A_BYTES, &tm_hi, fb, k, rb_b);
+        tma_load_block(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, rb_b + 1);
+        tma_load_block(sb + 2 * A_BYTES + B_BYTES, &tm_lo, fb, k, rb_b);
+        tma_load_block(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, rb_b + 1);
         issued[p_stage] = true;
         issued_parity[p_stage] = p_phase;
         if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
@@ -392,14 +395,18 @@ EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
+// The blocked copy as a 4-D tensor {32 columns, 128 rows, column blocks,
+// row blocks}; one box is one contiguous 8 KB block.
 cudaError_t encode_rows(const __nv_bfloat16 *base, int64_t n, int64_t Dp, CUtensorMap *m) {
   EncodeTiledFn fn = get_encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims,
+  const int64_t nkb = Dp / BK, nrb = (n + BM - 1) / BM;
+  cuuint64_t dims[4] = {(cuuint64_t)BK, (cuuint64_t)BM, (cuuint64_t)nkb, (cuuint64_t)nrb};
+  cuuint64_t strides[3] = {(cuuint64_t)BK * 2, (cuuint64_t)BK * BM * 2,
+                           (cuuint64_t)nkb * BK * BM * 2};
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)BM, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

@@ -22,6 +22,7 @@ namespace ap {
 namespace {
 
 constexpr int kStatsThreads = 512;
+constexpr int kSplitThreads = 256;
 
 __device__ __forceinline__ double block_sum_f64(double v, double *red) {
   // warp shuffle tree, then one warp over the per-warp sums
@@ -40,22 +41,21 @@ __device__ __forceinline__ double block_sum_f64(double v, double *red) {
   return r;
 }
 
-// One CTA per row: FP64 mean, then FP64 centred sum of squares.
+// Pass 1 of the load pipeline: one CTA per row, FP64 mean (FP32 partial sums
+// of 64 elements per thread folded into FP64).
 template <bool VEC4>
 __global__ void __launch_bounds__(kStatsThreads)
-vec_stats_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
-                 double *__restrict__ mu_out, double *__restrict__ ss_out,
-                 double *__restrict__ rs_out) {
+vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
+                double *__restrict__ mu_out) {
   __shared__ double red[33];
   for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
     const float *x = X + row * ld;
-    // pass 1: sum
     double acc = 0.0;
     float part = 0.f;
     int cnt = 0;
     if (VEC4) {
       const float4 *x4 = reinterpret_cast<const float4 *>(x);
-      int64_t n4 = D >> 2;
+      const int64_t n4 = D >> 2;
       for (int64_t k = threadIdx.x; k < n4; k += blockDim.x) {
         float4 v = __ldg(x4 + k);
         part += (v.x + v.y) + (v.z + v.w);
@@ -69,61 +69,35 @@ vec_stats_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
       }
     }
     acc += (double)part;
-    double mu = block_sum_f64(acc, red) / (double)D;
-    // pass 2: centred sum of squares
-    float mh = (float)mu;
-    float ml = (float)(mu - (double)mh);
-    acc = 0.0;
-    part = 0.f;
-    cnt = 0;
-    if (VEC4) {
-      const float4 *x4 = reinterpret_cast<const float4 *>(x);
-      int64_t n4 = D >> 2;
-      for (int64_t k = threadIdx.x; k < n4; k += blockDim.x) {
-        float4 v = __ldg(x4 + k);
-        float c0 = (v.x - mh) - ml, c1 = (v.y - mh) - ml;
-        float c2 = (v.z - mh) - ml, c3 = (v.w - mh) - ml;
-        part += (c0 * c0 + c1 * c1) + (c2 * c2 + c3 * c3);
-        if (++cnt == 16) { acc += (double)part; part = 0.f; cnt = 0; }
-      }
-      for (int64_t k = (n4 << 2) + threadIdx.x; k < D; k += blockDim.x) {
-        float c = (x[k] - mh) - ml;
-        part += c * c;
-      }
-    } else {
-      for (int64_t k = threadIdx.x; k < D; k += blockDim.x) {
-        float c = (__ldg(x + k) - mh) - ml;
-        part += c * c;
-        if (++cnt == 64) { acc += (double)part; part = 0.f; cnt = 0; }
-      }
-    }
-    acc += (double)part;
-    double ss = block_sum_f64(acc, red);
-    if (threadIdx.x == 0) {
-      mu_out[row] = mu;
-      ss_out[row] = ss;
-      // zero variance: correlation undefined, propagate NaN
-      rs_out[row] = ss > 0.0 ? 1.0 / sqrt(ss) : __longlong_as_double(0x7ff8000000000000ll);
-    }
+    const double mu = block_sum_f64(acc, red) / (double)D;
+    if (threadIdx.x == 0) mu_out[row] = mu;
   }
 }
 
-// Centre each row and write the split-BF16 (and optionally FP32) copies,
-// zero-padded to Dp columns.  Each thread handles 4 consecutive columns.
+// Pass 2: centre each row against its FP64 mean (as the two-float pair
+// mu_hi + mu_lo), write the blocked split-BF16 and/or FP32 copies (zero
+// padded to Dp columns) and this CTA's FP64 partial of sum_k c_k^2.
+// Grid: x = kSplitParts column ranges of a row, y = rows (strided).
 template <bool VEC4>
-__global__ void __launch_bounds__(256)
-vec_split_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld, int64_t Dp,
-                 const double *__restrict__ mu, __nv_bfloat16 *__restrict__ hi,
-                 __nv_bfloat16 *__restrict__ lo, float *__restrict__ c32) {
-  int64_t q4 = Dp >> 2;                       // float4 groups per padded row
-  for (int64_t row = blockIdx.y; row < n; row += gridDim.y) {
-    const float *x = X + row * ld;
-    double m = mu[row];
-    float mh = (float)m;
-    float ml = (float)(m - (double)mh);
+__global__ void __launch_bounds__(kSplitThreads)
+vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t n, int64_t D, int64_t ld,
+                 int64_t Dp, const double *__restrict__ mu, __nv_bfloat16 *__restrict__ hi,
+                 __nv_bfloat16 *__restrict__ lo, float *__restrict__ c32,
+                 double *__restrict__ part) {
+  __shared__ double red[33];
+  const int64_t q4 = Dp >> 2;                  // float4 groups per padded row
+  const int64_t nkb_tc = Dp / kTcKBlock, nkb_32 = Dp / kF32KBlock;
+  for (int64_t lr = blockIdx.y; lr < n; lr += gridDim.y) {
+    const int64_t row = row0 + lr;             // global item index
+    const float *x = X + lr * ld;
+    const double m = mu[row];
+    const float mh = (float)m;
+    const float ml = (float)(m - (double)mh);
+    double acc = 0.0;
+    float psum = 0.f;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q4;
          q += (int64_t)gridDim.x * blockDim.x) {
-      int64_t k = q << 2;
+      const int64_t k = q << 2;
       float v[4];
       if (VEC4 && k + 3 < D) {
         float4 t = __ldg(reinterpret_cast<const float4 *>(x + k));
@@ -135,7 +109,7 @@ vec_split_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld, 
       float c[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) c[e] = (k + e < D) ? (v[e] - mh) - ml : 0.f;
-      size_t o = (size_t)row * Dp + k;
+      psum += (c[0] * c[0] + c[1] * c[1]) + (c[2] * c[2] + c[3] * c[3]);
       if (hi) {
         __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -148,11 +122,35 @@ vec_split_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld, 
         hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
         lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
         lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+        const size_t o = blocked_offset(row, k, nkb_tc, kTcKBlock);
         *reinterpret_cast<uint2 *>(hi + o) = hv;
         *reinterpret_cast<uint2 *>(lo + o) = lv;
       }
-      if (c32) *reinterpret_cast<float4 *>(c32 + o) = make_float4(c[0], c[1], c[2], c[3]);
+      if (c32) {
+        const size_t o = blocked_offset(row, k, nkb_32, kF32KBlock);
+        *reinterpret_cast<float4 *>(c32 + o) = make_float4(c[0], c[1], c[2], c[3]);
+      }
+      // fold every 16 float4 (64 elements) into FP64
+      if (((q / ((int64_t)gridDim.x * blockDim.x)) & 15) == 15) { acc += (double)psum; psum = 0.f; }
     }
+    acc += (double)psum;
+    const double s = block_sum_f64(acc, red);
+    if (threadIdx.x == 0) part[row * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// ss_i = sum of the row's partials in a fixed order; rs_i = 1 / sqrt(ss_i)
+__global__ void vec_finalize_kernel(const double *__restrict__ part, int64_t row0, int64_t n,
+                                    int nparts, double *__restrict__ ss,
+                                    double *__restrict__ rs) {
+  for (int64_t lr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lr < n;
+       lr += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = row0 + lr;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[row * nparts + b];
+    ss[row] = s;
+    // zero variance: correlation undefined, propagate NaN
+    rs[row] = s > 0.0 ? 1.0 / sqrt(s) : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -175,7 +173,6 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
   __shared__ int s_tile;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int lrow = tid & 127, lh = tid >> 7;     // loader: row, k-quad pair
   const int64_t nk = Dp / kF32K;
 
   for (;;) {
@@ -186,9 +183,10 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
     if (t >= n_tiles) break;
     const int64_t i0 = (int64_t)tiles[2 * t] * kF32Tile;
     const int64_t j0 = (int64_t)tiles[2 * t + 1] * kF32Tile;
-    const bool a_ok = i0 + lrow < n, b_ok = j0 + lrow < n;
-    const float *arow = C + (a_ok ? (i0 + lrow) : 0) * Dp;
-    const float *brow = C + (b_ok ? (j0 + lrow) : 0) * Dp;
+    // blocked copy: block (row block, k block) = 128 rows x 16 columns, contiguous
+    const int64_t nkb = Dp / kF32KBlock;
+    const float4 *ablk = reinterpret_cast<const float4 *>(C + (size_t)(i0 >> 7) * nkb * 2048);
+    const float4 *bblk = reinterpret_cast<const float4 *>(C + (size_t)(j0 >> 7) * nkb * 2048);
 
     float acc[8][8];
 #pragma unroll
@@ -197,23 +195,21 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 
     float4 ra[2], rb[2];
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     auto gload = [&](int64_t kb) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int64_t k = kb * kF32K + (lh + 2 * h) * 4;
-        ra[h] = a_ok ? __ldg(reinterpret_cast<const float4 *>(arow + k)) : z4;
-        rb[h] = b_ok ? __ldg(reinterpret_cast<const float4 *>(brow + k)) : z4;
+        ra[h] = __ldg(ablk + kb * 512 + tid + 256 * h);
+        rb[h] = __ldg(bblk + kb * 512 + tid + 256 * h);
       }
     };
     auto sstore = [&](int buf) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int kq = (lh + 2 * h) * 4;
-        As[buf][kq + 0][lrow] = ra[h].x; As[buf][kq + 1][lrow] = ra[h].y;
-        As[buf][kq + 2][lrow] = ra[h].z; As[buf][kq + 3][lrow] = ra[h].w;
-        Bs[buf][kq + 0][lrow] = rb[h].x; Bs[buf][kq + 1][lrow] = rb[h].y;
-        Bs[buf][kq + 2][lrow] = rb[h].z; Bs[buf][kq + 3][lrow] = rb[h].w;
+        const int f = tid + 256 * h, r = f >> 2, kq = (f & 3) * 4;
+        As[buf][kq + 0][r] = ra[h].x; As[buf][kq + 1][r] = ra[h].y;
+        As[buf][kq + 2][r] = ra[h].z; As[buf][kq + 3][r] = ra[h].w;
+        Bs[buf][kq + 0][r] = rb[h].x; Bs[buf][kq + 1][r] = rb[h].y;
+        Bs[buf][kq + 2][r] = rb[h].z; Bs[buf][kq + 3][r] = rb[h].w;
       }
     };
 
@@ -260,27 +256,32 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
 
 }  // namespace
 
-cudaError_t launch_vec_stats(const float *X, int64_t n, int64_t D, int64_t ld, double *mu,
-                             double *ss, double *rs, cudaStream_t s) {
+cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, double *mu,
+                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int grid = (int)(n < 65535 ? n : 65535);
-  bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  if (vec4) vec_stats_kernel<true><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu, ss, rs);
-  else vec_stats_kernel<false><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu, ss, rs);
+  const int grid = (int)(n < 65535 ? n : 65535);
+  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (vec4) vec_mean_kernel<true><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu);
+  else vec_mean_kernel<false><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vec_split(const float *X, int64_t n, int64_t D, int64_t ld, int64_t Dp,
-                             const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                             float *c32, cudaStream_t s) {
+cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t n, int64_t D, int64_t ld,
+                             int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                             float *c32, double *part, double *ss, double *rs, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int64_t q4 = Dp >> 2;
-  int gx = (int)((q4 + 255) / 256);
-  if (gx > 1024) gx = 1024;
-  dim3 grid(gx, (unsigned)(n < 65535 ? n : 65535));
-  bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  if (vec4) vec_split_kernel<true><<<grid, 256, 0, s>>>(X, n, D, ld, Dp, mu, hi, lo, c32);
-  else vec_split_kernel<false><<<grid, 256, 0, s>>>(X, n, D, ld, Dp, mu, hi, lo, c32);
+  dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
+  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (vec4)
+    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(X, row0, n, D, ld, Dp, mu, hi, lo, c32,
+                                                          part);
+  else
+    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(X, row0, n, D, ld, Dp, mu, hi, lo,
+                                                           c32, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  vec_finalize_kernel<<<fg, 256, 0, s>>>(part, row0, n, kSplitParts, ss, rs);
   return cudaGetLastError();
 }
 
