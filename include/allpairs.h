@@ -215,6 +215,38 @@ int64_t ap_pair_index(int64_t i, int64_t j, int64_t n);
 ap_status ap_plan_tiles(int64_t n, int32_t block, int32_t *out, int64_t cap,
                         int64_t *n_tiles);
 
+/*
+ * ap_pearson_fp32_noalloc -- all-pairs Pearson correlation on the plain FP32
+ * CUDA-core path, for callers that cannot let the library allocate GPU
+ * memory (work recorded while a CUDA graph is being captured, processes whose
+ * device memory is handed out by their own pool allocator, services with a
+ * hard per-request memory limit).  The paper has no counterpart; this is an
+ * addition of this library.
+ *   data: device float[n_items][ld] (row-major, dim <= ld values per row,
+ *         ld = 0 means ld = dim), caller-owned, read only;
+ *   out:  device double[n_items(n_items-1)/2], packed as above, written.
+ * Same arithmetic as ap_run_pairs(AP_FN_PEARSON, AP_PREC_FP32): FP64 mean and
+ * norm per item, FP32 centring and Gram, FP64 scaling.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine: its working memory (item
+ * means, inverse norms, the tile-queue counter) is one file-scope
+ * `static __device__` array of AP_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * loading the library keeps until the process exits.
+ *   - At most AP_NOALLOC_MAX_ITEMS items; more returns AP_ERR_UNSUPPORTED
+ *     before any device work.  dim < 2, ld < dim, NULL data/out with n >= 2
+ *     return AP_ERR_INVALID_ARG.  n < 2 returns AP_OK and touches nothing.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array (its queue counter is reset at the start
+ *     of every call): calls whose work overlaps on the GPU -- on different
+ *     streams, or from different threads -- race and give wrong results.
+ *     Serialise them, e.g. on one stream.
+ */
+#define AP_NOALLOC_MAX_ITEMS 65536
+#define AP_NOALLOC_SCRATCH_BYTES (256 + 2 * 8 * AP_NOALLOC_MAX_ITEMS)
+ap_status ap_pearson_fp32_noalloc(const float *data, int64_t n_items, int64_t dim, int64_t ld,
+                                  double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
