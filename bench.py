@@ -315,8 +315,194 @@ def ours(args):
     return 0
 
 
+# SFU (MUFU) throughput of a GB300 SM, measured with independent chains of
+# each instruction: ex2.approx 30.2 and rcp.approx 15.2 results per clock;
+# the overlap kernels' roofline is 152 SMs x the SM clock seen during the run
+# x the point-pair rate these allow (one rcp and one ex2 per point pair)
+EX2_PER_CLK_PER_SM = 32
+RCP_PER_CLK_PER_SM = 16
+OOC_N, OOC_DIM, OOC_CACHE = 8192, 3 << 20, 48 << 30
+
+
+def run_ooc_workload(args):
+    """Out-of-core correlation: 8192 vectors of 3*2^20 FP32 (96 GiB) in pinned
+    host memory streamed through a 48 GiB HBM slot cache (the host's 199 GB of
+    RAM cannot hold the 16,384-vector, 192 GiB set pinned; set and cache are
+    both halved, keeping their ratio)."""
+    import torch
+    import synth
+    import paper_2009_04755_gb300 as ap
+    n, D = OOC_N, OOC_DIM
+    P = n * (n - 1) // 2
+    torch.cuda.set_device(0)
+    Xh = torch.empty(n, D, dtype=torch.float32, pin_memory=True)
+    chunk = 1024
+    for r0 in range(0, n, chunk):
+        Xd = synth.vectors_grouped(chunk, D, seed=1000 + r0 // chunk, device="cuda")
+        Xh[r0:r0 + chunk].copy_(Xd)
+        del Xd
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    # the host link as measured here (4 GiB pinned -> device)
+    # the host link as measured here: macro-sized (3 GiB) pinned -> device
+    # copies from eight places of the host set, best of them
+    macro = 256 * D
+    probe = torch.empty(macro, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flat = Xh.view(-1)
+    rates = []
+    for k in range(9):
+        off = (k * (n // 8) % (n - 256)) * D
+        e0.record()
+        probe.copy_(flat[off:off + macro], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        if k:
+            rates.append(macro * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    link_gbs = max(rates)
+    del probe
+    items = ap.Items.from_vectors(Xh, slot_cache_bytes=OOC_CACHE)
+    out = torch.empty(P, dtype=torch.float64, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        items.run_pairs(out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        items.run_pairs(out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = items.stats()
+    h2d_gbs = st["h2d_bytes"] / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": P / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
+            "config": {"workload": "pearson_ooc_n8192_d3145728", "n_items": n, "dim": D,
+                       "host_bytes": n * D * 4, "slot_cache_bytes": OOC_CACHE},
+            "reuse_R": st["reuse_R"], "slot_hit_rate": st["slot_hit_rate"],
+            "h2d_bytes_per_step": st["h2d_bytes"], "h2d_gbs": h2d_gbs,
+            "roofline": {"bound": "link", "achieved": h2d_gbs, "peak": link_gbs,
+                         "unit": "GB/s", "frac": h2d_gbs / link_gbs, "traffic": None,
+                         "peak_kind": "best of 8 macro-sized pinned H2D copies in this run"},
+            "link_probe_gbs": {"min": min(rates), "median": statistics.median(rates),
+                               "max": max(rates)},
+            "compulsory_link_frac": (n * D * 4) / (ms / 1e3) / 1e9 / link_gbs}
+    if clk:
+        line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    items.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cloud_workload(args):
+    """Point-cloud workloads: overlap cost (2-D n=256, 3-D lognormal n=20000)
+    and batched registration (2-D n=1024, 20 fused ascent steps per step)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2009_04755_gb300 as ap
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = args.workload
+    if wl == "overlap2d_n256":
+        c = synth.clouds_uniform(n=256, dim=2, size=(64, 128), seed=0)
+    elif wl == "overlap3d_n20000":
+        c = synth.clouds_lognormal(n=20000, dim=3, seed=0)
+    else:
+        c = synth.clouds_templates(n=1024, seed=0)
+    n = len(c["offsets"]) - 1
+    P = n * (n - 1) // 2
+    sizes = np.diff(c["offsets"]).astype(np.float64)
+    point_pairs = (sizes.sum() ** 2 - (sizes ** 2).sum()) / 2
+    items = ap.Items.from_clouds(c)
+    tuned = items.tune(1 if wl == "register2d_n1024" else 0)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(P, dtype=torch.float32, device="cuda")
+    n_asc = 20
+    prm = torch.zeros(P, 3, device="cuda")
+
+    def step():
+        if wl == "register2d_n1024":
+            prm.zero_()
+            items.ascent(prm, n_asc, 1e-3)
+        else:
+            items.run_pairs(ap.AP_FN_OVERLAP, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    units = P * (n_asc if wl == "register2d_n1024" else 1)
+    mufu = 2.0 * point_pairs * (n_asc if wl == "register2d_n1024" else 1)
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    # one rcp (16/clk/SM) and one ex2 (32/clk/SM) per point pair: 2 MUFU
+    # results per 3/32 clock per SM
+    peak = 2.0 / (1.0 / RCP_PER_CLK_PER_SM + 1.0 / EX2_PER_CLK_PER_SM) * 152 * sm_mhz * 1e6 / 1e12
+    achieved = mufu / (ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": units / (ms / 1e3),
+            "unit": "pair-steps/s" if wl == "register2d_n1024" else "pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl, "n_items": n, "pairs": P, "point_pairs": point_pairs,
+                       "plan": tuned},
+            "point_pairs_per_s": point_pairs * (n_asc if wl == "register2d_n1024" else 1)
+            / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TMUFU/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "overlap_kernel",
+                         "peak_kind": "16 MUFU/clk/SM x 152 SMs x median SM clock"},
+            "gpu_launches": args.steps * (n_asc if wl == "register2d_n1024" else 1)}
+    if clk:
+        line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(7)
+        k = args.ref_pairs
+        pi = rng.integers(0, n - 1, 4 * k)
+        pj = rng.integers(0, n, 4 * k)
+        keep = pi < pj
+        pi, pj = pi[keep][:k], pj[keep][:k]
+        cores = os.cpu_count() or 1
+        oracle.build()
+        t0 = time.perf_counter()
+        if wl == "register2d_n1024":
+            f_ref, _ = oracle.overlap_grad(c, pi, pj, None, n_threads=cores)
+        else:
+            f_ref = oracle.overlap(c, pi, pj, n_threads=cores)
+        secs = time.perf_counter() - t0
+        items.run_pairs(ap.AP_FN_OVERLAP, out=out)
+        p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+        got = out[p].double().cpu().numpy()
+        line["max_rel_err_sampled"] = float((np.abs(got - f_ref) / np.abs(f_ref)).max())
+        line["cpu_baseline"] = {"value": len(pi) / secs, "unit": "pairs/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{len(pi)} random pairs of the workload"}
+    items.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--workload", default="pearson_n8192_d1048576",
+                    choices=["pearson_n8192_d1048576", "overlap2d_n256", "overlap3d_n20000",
+                             "register2d_n1024", "pearson_ooc_n8192_d3145728"])
+    ap.add_argument("--ref-pairs", type=int, default=2000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -329,6 +515,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "pearson_ooc_n8192_d3145728":
+        return run_ooc_workload(args)
+    if args.workload != "pearson_n8192_d1048576":
+        return run_cloud_workload(args)
     return ours(args)
 
 

@@ -115,6 +115,19 @@ typedef struct ap_run_stats {
   int32_t reserved;
 } ap_run_stats;
 
+/* Tile plan of a point-cloud set: blocks of at most block_items items and
+ * block_pts padded points (one block is staged in shared memory per tile),
+ * reg_r a-points held per lane (chunks of 32*reg_r points).  sorted = items
+ * stored largest first (decided at creation).  rate = point pairs per second
+ * the tuner measured for the chosen plan. */
+typedef struct ap_plan {
+  int32_t block_items;
+  int32_t block_pts;
+  int32_t reg_r;
+  int32_t sorted;
+  double rate;
+} ap_plan;
+
 /*
  * ap_create_items -- run the load pipeline l(i) for every item (Sec. III:
  * transfer to the GPU and pre-process there) into library-owned storage.

@@ -43,6 +43,11 @@ class RunStats(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class Plan(ctypes.Structure):
+    _fields_ = [("block_items", ctypes.c_int32), ("block_pts", ctypes.c_int32),
+                ("reg_r", ctypes.c_int32), ("sorted", ctypes.c_int32), ("rate", ctypes.c_double)]
+
+
 class APError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -73,6 +78,11 @@ def lib():
             "ap_pair_count": (i64, [i64]),
             "ap_pair_index": (i64, [i64, i64, i64]),
             "ap_plan_tiles": (i32, [i64, i32, vp, i64, ctypes.POINTER(i64)]),
+            "ap_tune": (i32, [vp, i32, vp, ctypes.POINTER(Plan)]),
+            "ap_get_plan": (i32, [vp, ctypes.POINTER(Plan)]),
+            "ap_set_plan": (i32, [vp, ctypes.POINTER(Plan)]),
+            "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -115,6 +125,15 @@ def plan_tiles(n: int, block: int):
     check(lib().ap_plan_tiles(int(n), int(block), out.ctypes.data, cnt.value, ctypes.byref(cnt)),
           "ap_plan_tiles")
     return out[:2 * cnt.value].reshape(-1, 2)
+
+
+def plan_out_of_core(n: int, dim: int, slot_cache_bytes: int) -> dict:
+    """Host-only preview of the out-of-core schedule (slots, loads, steps)."""
+    s, l, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ap_plan_out_of_core(int(n), int(dim), int(slot_cache_bytes), ctypes.byref(s),
+                                    ctypes.byref(l), ctypes.byref(t)), "ap_plan_out_of_core")
+    return {"slots": s.value, "loads": l.value, "steps": t.value,
+            "macros": (int(n) + 255) // 256}
 
 
 def _stream_ptr(stream):
@@ -171,8 +190,12 @@ class Items:
         return cls(h, d.kind, n)
 
     @classmethod
-    def from_vectors(cls, X, precisions=(AP_PREC_SPLIT_BF16,), stream=None) -> "Items":
-        """X: torch float32 [n, D] on the GPU, or on the host (ideally pinned)."""
+    def from_vectors(cls, X, precisions=(AP_PREC_SPLIT_BF16,), stream=None,
+                     slot_cache_bytes: int = 0) -> "Items":
+        """X: torch float32 [n, D] on the GPU, or on the host (ideally pinned).
+        slot_cache_bytes > 0 (host X only): out-of-core mode; X must stay alive
+        (and unchanged between runs unless that is intended) while the handle
+        exists."""
         import torch
         assert X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
         d = ItemsDesc()
@@ -183,10 +206,14 @@ class Items:
         d.dim = X.shape[1]
         d.ld = X.stride(0)
         d.precisions = sum(1 << p for p in precisions)
+        d.slot_cache_bytes = int(slot_cache_bytes)
         h = ctypes.c_void_p()
         check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
               "ap_create_items")
-        return cls(h, AP_ITEMS_VECTOR, X.shape[0])
+        obj = cls(h, AP_ITEMS_VECTOR, X.shape[0])
+        if slot_cache_bytes:
+            obj._keep.append(X)          # the library reads it on every run
+        return obj
 
     def update(self, X, stream=None):
         check(lib().ap_update_items(self._h, _ptr(X), 0 if X.is_cuda else 1, _stream_ptr(stream)),
@@ -223,6 +250,21 @@ class Items:
         check(lib().ap_ascent(self._h, _ptr(params), int(n_steps), float(eta), float(fmin),
                               _ptr(f), _ptr(flags), _stream_ptr(stream)), "ap_ascent")
         return params, f[:self.P], flags[:self.P]
+
+    def tune(self, mode: int = 0, stream=None) -> dict:
+        """Autotune the tile plan (clouds); returns the chosen plan."""
+        p = Plan()
+        check(lib().ap_tune(self._h, int(mode), _stream_ptr(stream), ctypes.byref(p)), "ap_tune")
+        return {k: getattr(p, k) for k, _ in Plan._fields_}
+
+    def plan(self) -> dict:
+        p = Plan()
+        check(lib().ap_get_plan(self._h, ctypes.byref(p)), "ap_get_plan")
+        return {k: getattr(p, k) for k, _ in Plan._fields_}
+
+    def set_plan(self, block_items: int, block_pts: int, reg_r: int):
+        p = Plan(int(block_items), int(block_pts), int(reg_r), 0, 0.0)
+        check(lib().ap_set_plan(self._h, ctypes.byref(p)), "ap_set_plan")
 
     def stats(self) -> dict:
         st = RunStats()

@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -67,6 +68,15 @@ struct CloudStore {
   int64_t tiles_cap = 0;
 };
 
+// one macro pair (a <= b) of an out-of-core batch and the slots holding them
+struct OocPair { int32_t a, b, slot_a, slot_b; };
+// one step of the out-of-core schedule: loads (macro, slot), then a Gram batch
+struct OocStep {
+  std::vector<std::pair<int32_t, int32_t>> loads;
+  std::vector<OocPair> pairs;
+  int64_t unit0 = 0, n_units = 0, cover0 = 0, n_cover = 0;
+};
+
 // ---------------------------------------------------------------------------
 // dense-vector storage
 // ---------------------------------------------------------------------------
@@ -81,10 +91,19 @@ struct VecStore {
   float *d_c32 = nullptr;                                      // [n][Dp]
   float *d_stage = nullptr;         // raw rows staged from the host
   int64_t stage_rows = 0;
-  // out-of-core mode
+  // out-of-core mode: HBM slot cache of 256-item macros
   bool out_of_core = false;
   const float *h_src = nullptr;
   uint64_t slot_cache_bytes = 0;
+  int64_t n_macros = 0, n_slots = 0, group = 0, ring = 0;
+  __nv_bfloat16 *d_pool_hi = nullptr, *d_pool_lo = nullptr;   // slot pool, blocked layout
+  float *d_raw = nullptr;                                      // raw staging ring
+  std::vector<cudaEvent_t> ev_raw_ready, ev_raw_free;
+  std::vector<int> ring_used;
+  std::vector<OocStep> steps;
+  int32_t *d_units = nullptr, *d_cover_units = nullptr;
+  void *tmap_pool_hi = nullptr, *tmap_pool_lo = nullptr;
+  int64_t ooc_loads = 0, ooc_uses = 0;
   // tile plans
   int32_t *d_tiles_tc = nullptr;  int64_t n_tiles_tc = 0;
   int32_t *d_tiles_f32 = nullptr; int64_t n_tiles_f32 = 0;
@@ -92,6 +111,25 @@ struct VecStore {
   double *d_g64 = nullptr;          // FP64 partial sums of the tensor-core Gram
 };
 
+}  // namespace ap
+
+namespace ap {
+// a captured launch sequence, replayed with cudaGraphLaunch
+struct GraphKey {
+  int32_t kind;                    // 1 overlap, 2 coverage, 3 ascent
+  const void *a, *b, *c, *d;       // buffers the sequence reads / writes
+  float eta, fmin;
+  int32_t n;
+  bool operator==(const GraphKey &o) const {
+    return kind == o.kind && a == o.a && b == o.b && c == o.c && d == o.d && eta == o.eta &&
+           fmin == o.fmin && n == o.n;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  uint64_t plan_version;
+  cudaGraphExec_t exec;
+};
 }  // namespace ap
 
 struct ap_items {
@@ -106,7 +144,10 @@ struct ap_items {
   ap_run_stats stats{};
   int32_t last_dev_error = 0;
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t graph_stream = nullptr;   // private stream the graphs are captured on
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  uint64_t plan_version = 0;
+  std::vector<ap::GraphEntry> graphs;
 };
 
 namespace ap {
@@ -143,7 +184,7 @@ __host__ __device__ __forceinline__ size_t blocked_offset(int64_t row, int64_t k
 cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, double *mu,
                             cudaStream_t s);
 // rows [row0, row0 + n) of the item set, X pointing at row row0
-cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t n, int64_t D, int64_t ld,
+cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D, int64_t ld,
                              int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                              float *c32, double *part, double *ss, double *rs, cudaStream_t s);
 cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
@@ -158,7 +199,11 @@ cudaError_t make_tc_tensor_maps(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo
 cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
                            const double *rs, const int32_t *tiles, int64_t n_tiles,
                            int32_t *queue, int32_t *status, double *g64, void *out,
-                           int coverage, cudaStream_t s);
+                           int coverage, int ooc, cudaStream_t s);
+// out-of-core unit: {A row block, B row blocks (2), I block, J block, chunk
+// begin, chunk end, unused}; chunks are 64 columns of D
+constexpr int kOocTileInts = 8;
+constexpr int kOocChunkCols = 64;
 // CTAs of one Gram launch and the FP64 scratch (doubles) it needs: one
 // 128 x 256 FP64 partial-sum tile per CTA
 int64_t tc_grid(int64_t n_tiles);
@@ -183,5 +228,43 @@ cudaError_t launch_cloud_pack(const float *x, const float *y, const float *z,
                               float4 *pts, float *lw, cudaStream_t s);
 
 int num_sms();
+
+// ---------------------------------------------------------------------------
+// shared host helpers (api.cu, tune.cu)
+// ---------------------------------------------------------------------------
+ap_status from_cuda(cudaError_t e);
+#define AP_TRY(expr)                               \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return ::ap::from_cuda(_e); \
+  } while (0)
+template <typename T>
+cudaError_t dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree(reinterpret_cast<void *>(p));
+  p = nullptr;
+}
+
+struct CloudPlanChoice { int32_t block_items, block_pts, reg_r; bool sorted; };
+CloudPlanChoice choose_cloud_plan(const CloudStore &c);
+ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch);
+// smallest a-points-per-lane that keeps the largest item within the row jobs
+int32_t min_reg_r(const CloudStore &c);
+
+// Launch `seq` on `s` through a cached CUDA graph captured on the handle's
+// private stream (direct launch when `s` is itself being captured).
+ap_status run_graphed(ap_items *it, const GraphKey &key, cudaStream_t s,
+                      const std::function<cudaError_t(cudaStream_t)> &seq);
+void clear_graphs(ap_items *it);
+
+// out-of-core vector sets (slotcache.cu)
+ap_status create_out_of_core(const ap_items_desc *d, ap_items *it);
+ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s);
+void free_out_of_core(VecStore &v);
 
 }  // namespace ap

@@ -31,32 +31,13 @@ int num_sms() {
   return cached;
 }
 
-namespace {
-
 ap_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return AP_OK;
-  cudaGetLastError();   // clear a sticky-free error so later calls can run
+  cudaGetLastError();   // clear a non-sticky error so later calls can run
   return e == cudaErrorMemoryAllocation ? AP_ERR_OOM : AP_ERR_CUDA;
 }
 
-#define AP_TRY(expr)                          \
-  do {                                        \
-    cudaError_t _e = (expr);                  \
-    if (_e != cudaSuccess) return from_cuda(_e); \
-  } while (0)
-
-template <typename T>
-cudaError_t dmalloc(T **p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return cudaSuccess;
-  return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
-}
-
-template <typename T>
-void dfree(T *&p) {
-  if (p) cudaFree(reinterpret_cast<void *>(p));
-  p = nullptr;
-}
+namespace {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -68,21 +49,24 @@ void free_items(ap_items *it) {
   VecStore &v = it->vec;
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
+  free_out_of_core(v);
   free_tc_tensor_maps(v.tmap_hi, v.tmap_lo);
   v.tmap_hi = v.tmap_lo = nullptr;
   dfree(it->d_queue);
   dfree(it->d_scratch);
+  clear_graphs(it);
+  if (it->graph_stream) cudaStreamDestroy(it->graph_stream);
   if (it->copy_stream) cudaStreamDestroy(it->copy_stream);
   for (cudaEvent_t *e : {&it->ev_a, &it->ev_b})
     if (*e) cudaEventDestroy(*e);
   delete it;
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // point clouds
 // ---------------------------------------------------------------------------
-struct CloudPlanChoice { int32_t block_items, block_pts, reg_r; bool sorted; };
-
 CloudPlanChoice choose_cloud_plan(const CloudStore &c) {
   CloudPlanChoice ch{};
   int64_t mx = 0, mn = INT64_MAX;
@@ -92,8 +76,7 @@ CloudPlanChoice choose_cloud_plan(const CloudStore &c) {
   // original order to know which item of a pair is moved)
   ch.sorted = (c.dim == 3) && mx > 4 * std::max<int64_t>(mn, 1);
   // a-points per lane: enough chunk width for the largest item
-  ch.reg_r = 2;
-  while ((int64_t)ch.reg_r * 32 * kOverlapMaxRowJobs < mx && ch.reg_r < 4) ch.reg_r *= 2;
+  ch.reg_r = std::max<int32_t>(2, min_reg_r(c));
   ch.block_pts = 4096;
   // block size: enough tiles to keep every SM busy several times over
   const int64_t want_tiles = (int64_t)num_sms() * 16;
@@ -131,8 +114,11 @@ ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
   it->stats.tile_m = ch.block_items;
   it->stats.tile_n = ch.block_items;
   it->stats.order = 0;
+  ++it->plan_version;
   return AP_OK;
 }
+
+namespace {
 
 ap_status create_clouds(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   CloudStore &c = it->cl;
@@ -219,7 +205,7 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
   const bool f32 = (v.precisions & (1u << AP_PREC_FP32)) != 0;
   if (!on_host) {
     AP_TRY(launch_vec_mean(data, v.n, v.D, v.ld, v.d_mu, s));
-    AP_TRY(launch_vec_split(data, 0, v.n, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
+    AP_TRY(launch_vec_split(data, 0, 0, v.n, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
                             split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
                             v.d_rs, s));
     return AP_OK;
@@ -249,7 +235,7 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[b], 0);
     if (e == cudaSuccess) e = launch_vec_mean(stage, nr, v.D, v.ld, v.d_mu + r0, s);
     if (e == cudaSuccess)
-      e = launch_vec_split(stage, r0, nr, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
+      e = launch_vec_split(stage, r0, r0, nr, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
                            v.d_rs, s);
     if (e == cudaSuccess) e = cudaEventRecord(done[b], s);
@@ -274,13 +260,14 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   v.precisions = d->precisions ? d->precisions : (1u << AP_PREC_SPLIT_BF16);
   if (v.precisions & ~((1u << AP_PREC_FP32) | (1u << AP_PREC_SPLIT_BF16)))
     return AP_ERR_INVALID_ARG;
-  if (d->slot_cache_bytes) return AP_ERR_UNSUPPORTED;   // out-of-core: see slotcache
   v.Dp = round_up(v.D, 64);
   const int64_t nn = std::max<int64_t>(v.n, 1);
   AP_TRY(dmalloc(&v.d_mu, nn));
   AP_TRY(dmalloc(&v.d_ss, nn));
   AP_TRY(dmalloc(&v.d_rs, nn));
   AP_TRY(dmalloc(&v.d_part, (size_t)nn * kSplitParts));
+  // out-of-core: items stay in host memory and stream through the slot cache
+  if (d->slot_cache_bytes) return create_out_of_core(d, it);
   // blocked copies cover whole row blocks; the padding rows stay zero
   v.n_rows_alloc = round_up(nn, kRowBlock);
   const size_t elems = (size_t)v.n_rows_alloc * v.Dp;
@@ -375,6 +362,7 @@ ap_status ap_create_items(const ap_items_desc *desc, void *stream, ap_items **ou
   cudaError_t e = dmalloc(&it->d_queue, 64);
   if (e == cudaSuccess) e = cudaMemset(it->d_queue, 0, 64 * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&it->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&it->graph_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&it->ev_a, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&it->ev_b, cudaEventDisableTiming);
   if (e != cudaSuccess) st = from_cuda(e);
@@ -418,6 +406,10 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   if (n < 2) return AP_OK;
   if (!out) return AP_ERR_INVALID_ARG;
   const int cover = fn == AP_FN_COVERAGE;
+  if (it->kind == AP_ITEMS_VECTOR && it->vec.out_of_core) {
+    if (!cover && precision != AP_PREC_SPLIT_BF16) return AP_ERR_STATE;
+    return run_out_of_core(it, out, cover, s);
+  }
   if (it->kind == AP_ITEMS_VECTOR) {
     VecStore &v = it->vec;
     const bool have_split = v.d_hi != nullptr, have_f32 = v.d_c32 != nullptr;
@@ -427,7 +419,7 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
     if (!use_split && !have_f32) return AP_ERR_STATE;
     if (use_split) {
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_tiles_tc, v.n_tiles_tc,
-                            it->d_queue, it->d_status, v.d_g64, out, cover, s));
+                            it->d_queue, it->d_status, v.d_g64, out, cover, 0, s));
       it->stats.tiles = v.n_tiles_tc;
       it->stats.tile_m = kTcTileM;
       it->stats.tile_n = kTcTileN;
@@ -443,7 +435,14 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
     it->stats.slot_hit_rate = 1.0;
     return AP_OK;
   }
-  AP_TRY(launch_overlap(it->cl, params, reinterpret_cast<float *>(out), cover, it->d_queue, s));
+  {
+    GraphKey key{1 + cover, params, out, nullptr, nullptr, 0.f, 0.f, 1};
+    ap_items *h = it;
+    ap_status st = run_graphed(it, key, s, [h, params, out, cover](cudaStream_t cs) {
+      return launch_overlap(h->cl, params, reinterpret_cast<float *>(out), cover, h->d_queue, cs);
+    });
+    if (st != AP_OK) return st;
+  }
   it->stats.tiles = it->cl.n_tiles;
   it->stats.item_loads = it->cl.n;
   it->stats.reuse_R = 1.0;
@@ -469,10 +468,17 @@ ap_status ap_ascent(ap_items *it, float *params, int32_t n_steps, float eta, flo
   if (it->cl.n < 2 || n_steps == 0) return AP_OK;
   if (!params) return AP_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  for (int32_t k = 0; k < n_steps; ++k)
-    AP_TRY(launch_overlap_grad_q(it->cl, it->d_queue, nullptr, nullptr, nullptr, f_out, eta, fmin,
-                                 params, flags, s));
-  return AP_OK;
+  // the n_steps fused steps are replayed as one CUDA graph
+  GraphKey key{3, params, f_out, flags, nullptr, eta, fmin, n_steps};
+  ap_items *h = it;
+  return run_graphed(it, key, s, [h, params, n_steps, eta, fmin, f_out, flags](cudaStream_t cs) {
+    for (int32_t k = 0; k < n_steps; ++k) {
+      cudaError_t e = launch_overlap_grad_q(h->cl, h->d_queue, nullptr, nullptr, nullptr, f_out,
+                                            eta, fmin, params, flags, cs);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  });
 }
 
 ap_status ap_destroy(ap_items *it) {

@@ -157,7 +157,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // (two accumulators, double-buffered), so the tensor core never carries a
 // long FP32 chain; eight epilogue warps drain each chunk into FP32 register
 // sums and fold those into FP64 scratch every kFlushChunks chunks.
-template <int COVER>
+//
+// OOC = 1 (out-of-core units): each entry of `tiles` is kOocTileInts int32
+// {row block of A, row blocks of B (two), I block, J block, first chunk, end
+// chunk} -- row blocks index the slot pool the tensor maps cover, I/J the
+// item grid -- and the epilogue adds the unit's partial Gram into FP64
+// `out` (atomically: several K ranges of one tile may run at once).
+template <int COVER, int OOC>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                int64_t n, int64_t Dp, const double *__restrict__ rs,
@@ -212,7 +218,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
 #pragma unroll
   for (int s = 0; s < STAGES; ++s) { issued[s] = false; issued_parity[s] = 0; }
   const int64_t nk = Dp / BK;
-  const int64_t nchunks = COVER ? 0 : nk / kChunkStages;
   double *my_g64 = g64 + (size_t)blockIdx.x * (BN * BM);
 
   for (;;) {
@@ -224,13 +229,27 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     __syncthreads();
     const int64_t t = *s_tile;
     if (t >= n_tiles) break;
-    const int32_t i0 = tiles[2 * t] * BM;
-    const int32_t j0 = tiles[2 * t + 1] * BN;
-    const int32_t rb_a = tiles[2 * t], rb_b = tiles[2 * t + 1] * (BN / BM);
+    int32_t i0, j0, rb_a, rb_b, rb_b1;
+    int64_t c_begin = 0, nchunks = COVER ? 0 : nk / kChunkStages;
+    if (OOC) {
+      const int32_t *u = tiles + (size_t)kOocTileInts * t;
+      rb_a = u[0]; rb_b = u[1]; rb_b1 = u[2];
+      i0 = u[3] * BM;
+      j0 = u[4] * BN;
+      c_begin = u[5];
+      nchunks = COVER ? 0 : (int64_t)(u[6] - u[5]);
+    } else {
+      i0 = tiles[2 * t] * BM;
+      j0 = tiles[2 * t + 1] * BN;
+      rb_a = tiles[2 * t];
+      rb_b = tiles[2 * t + 1] * (BN / BM);
+      rb_b1 = rb_b + 1;
+    }
 
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
-      for (int64_t kb = 0; kb < nchunks * kChunkStages; ++kb) {
+      const int64_t kb0 = c_begin * kChunkStages;
+      for (int64_t kb = kb0; kb < kb0 + nchunks * kChunkStages; ++kb) {
         if (!mbar_wait(empty_bar(p_stage), p_phase ^ 1, s_abort)) {
           atomicCAS(status, 0, DEV_TIMEOUT_EMPTY);
           *s_abort = 1;
@@ -243,9 +262,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         tma_load_block(sb, &tm_hi, fb, k, rb_a);
         tma_load_block(sb + A_BYTES, &tm_lo, fb, k, rb_a);
         tma_load_block(sb + 2 * A_BYTES, &tm_hi, fb, k, rb_b);
-        tma_load_block(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, rb_b + 1);
+        tma_load_block(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, rb_b1);
         tma_load_block(sb + 2 * A_BYTES + B_BYTES, &tm_lo, fb, k, rb_b);
-        tma_load_block(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, rb_b + 1);
+        tma_load_block(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, rb_b1);
         issued[p_stage] = true;
         issued_parity[p_stage] = p_phase;
         if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
@@ -335,7 +354,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       }
       ok = ok && !*s_abort;
       if (ok && i < n) {
-        const double ri = COVER ? 0.0 : rs[i];
+        const double ri = (COVER || OOC) ? 0.0 : rs[i];
         const int64_t jb = (int64_t)j0 + h * (BN / 2);
         int64_t p = pair_index(i, jb > i ? jb : i + 1, n);
 #pragma unroll
@@ -347,7 +366,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             } else {
               double g = (double)sum[e];
               if (flushed) g += my_g64[(size_t)(h * (BN / 2) + e) * BM + row];
-              reinterpret_cast<double *>(out)[p] = g * ri * rs[j];
+              if (OOC) atomicAdd(reinterpret_cast<double *>(out) + p, g);
+              else reinterpret_cast<double *>(out)[p] = g * ri * rs[j];
             }
             ++p;
           }
@@ -444,15 +464,19 @@ void free_tc_tensor_maps(void *a, void *b) {
 cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
                            const double *rs, const int32_t *tiles, int64_t n_tiles,
                            int32_t *queue, int32_t *status, double *g64, void *out,
-                           int coverage, cudaStream_t s) {
+                           int coverage, int ooc, cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
-  static bool attr_done[2] = {false, false};
-  auto kern = coverage ? gram_tc_kernel<1> : gram_tc_kernel<0>;
-  if (!attr_done[coverage ? 1 : 0]) {
+  static bool attr_done[4] = {false, false, false, false};
+  const int v = (coverage ? 1 : 0) + (ooc ? 2 : 0);
+  void (*kern)(CUtensorMap, CUtensorMap, int64_t, int64_t, const double *, const int32_t *,
+               int64_t, int32_t *, int32_t *, double *, void *) =
+      v == 0 ? gram_tc_kernel<0, 0> : v == 1 ? gram_tc_kernel<1, 0>
+             : v == 2 ? gram_tc_kernel<0, 1> : gram_tc_kernel<1, 1>;
+  if (!attr_done[v]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    attr_done[coverage ? 1 : 0] = true;
+    attr_done[v] = true;
   }
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;

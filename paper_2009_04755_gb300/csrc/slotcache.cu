@@ -1,0 +1,313 @@
+// slotcache.cu -- out-of-core vector sets: an HBM slot cache refilled
+// asynchronously from page-locked host memory (the first-level device cache
+// of Sec. IV-A with the asynchronous, overlapped loading of Sec. IV-C).
+//
+// Unit of caching: a "macro" of 256 consecutive items, stored pre-processed
+// (split-BF16 hi/lo, blocked layout) in one slot of a pool; the Gram's tile
+// (128 items x 256 items) reads its A half-macro and its B macro straight out
+// of the pool through 4-D tensor maps whose row-block coordinate is
+// 2*slot + half.
+//
+// Schedule (host, computed once, the future fully known): a resident set A
+// of S - g macros is loaded and its pairs computed, then the remaining
+// macros stream through the other g slots in groups; every pair of A with
+// the streamed groups is done on the way, and the remaining macros are
+// handled the same way.  A slot is given up by the macro needed farthest in
+// the future (or never again), which is the schedule-aware form of the
+// paper's least-recently-used eviction.  A load is: copy the macro's raw FP32
+// rows from the host into a staging ring (copy stream), then pre-process them
+// into the slot on the compute stream.  Copies for the next group run while
+// the current group's Gram runs; the compute stream only waits for its own
+// loads.  Each batch's tiles are split along D into units so even a small
+// batch fills every SM; units add their FP64 partial Gram into the packed
+// output, and a final pass scales by 1 / sqrt(ss_i ss_j).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <numeric>
+#include <set>
+#include <vector>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr int64_t kMacro = 2 * kRowBlock;   // items per slot
+
+__global__ void ooc_finalize_kernel(double *__restrict__ out, const double *__restrict__ rs,
+                                    int64_t n) {
+  for (int64_t i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    const double ri = rs[i];
+    const int64_t p0 = pair_index(i, i + 1, n);
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x)
+      out[p0 + (j - i - 1)] *= ri * rs[j];
+  }
+}
+
+}  // namespace
+
+void free_out_of_core(VecStore &v) {
+  dfree(v.d_pool_hi);
+  dfree(v.d_pool_lo);
+  dfree(v.d_raw);
+  dfree(v.d_units);
+  dfree(v.d_cover_units);
+  for (cudaEvent_t e : v.ev_raw_ready) cudaEventDestroy(e);
+  for (cudaEvent_t e : v.ev_raw_free) cudaEventDestroy(e);
+  v.ev_raw_ready.clear();
+  v.ev_raw_free.clear();
+  free_tc_tensor_maps(v.tmap_pool_hi, v.tmap_pool_lo);
+  v.tmap_pool_hi = v.tmap_pool_lo = nullptr;
+}
+
+// Build the load / compute schedule for M macros and S slots.
+static void build_schedule(VecStore &v) {
+  const int64_t M = v.n_macros, S = v.n_slots, g = v.group;
+  std::vector<int64_t> slot_of(M, -1), macro_in(S, -1);
+  std::vector<int64_t> undone(M);
+  std::iota(undone.begin(), undone.end(), 0);
+  v.steps.clear();
+
+  // position of each macro in the remaining order (for farthest-next-use eviction)
+  auto load = [&](int64_t m, const std::set<int64_t> &keep, const std::vector<int64_t> &order,
+                  OocStep &st) {
+    if (slot_of[m] >= 0) return;
+    int64_t victim = -1, best_rank = -1;
+    std::vector<int64_t> rank(M, -1);
+    for (size_t k = 0; k < order.size(); ++k) rank[order[k]] = (int64_t)k;
+    for (int64_t s = 0; s < S; ++s) {
+      const int64_t o = macro_in[s];
+      if (o < 0) { victim = s; break; }                  // a free slot
+      if (keep.count(o)) continue;
+      const int64_t r = rank[o] < 0 ? INT64_MAX : rank[o];  // never needed again: best
+      if (r > best_rank) { best_rank = r; victim = s; }
+    }
+    if (macro_in[victim] >= 0) slot_of[macro_in[victim]] = -1;
+    macro_in[victim] = m;
+    slot_of[m] = victim;
+    st.loads.push_back({(int32_t)m, (int32_t)victim});
+  };
+  auto pairs_among = [&](const std::vector<int64_t> &a, const std::vector<int64_t> &b,
+                         bool same, OocStep &st) {
+    for (size_t x = 0; x < a.size(); ++x)
+      for (size_t y = same ? x : 0; y < b.size(); ++y) {
+        const int64_t p = std::min(a[x], b[y]), q = std::max(a[x], b[y]);
+        st.pairs.push_back({(int32_t)p, (int32_t)q, (int32_t)slot_of[p], (int32_t)slot_of[q]});
+      }
+  };
+
+  while (!undone.empty()) {
+    // resident macros first: they cost no load
+    std::stable_partition(undone.begin(), undone.end(),
+                          [&](int64_t m) { return slot_of[m] >= 0; });
+    if ((int64_t)undone.size() <= S) {
+      OocStep st;
+      std::set<int64_t> keep(undone.begin(), undone.end());
+      for (int64_t m : undone) load(m, keep, undone, st);
+      pairs_among(undone, undone, true, st);
+      v.steps.push_back(st);
+      break;
+    }
+    std::vector<int64_t> A(undone.begin(), undone.begin() + (S - g));
+    std::vector<int64_t> rest(undone.begin() + (S - g), undone.end());
+    std::vector<int64_t> order = A;
+    order.insert(order.end(), rest.begin(), rest.end());
+    {
+      OocStep st;
+      std::set<int64_t> keep(A.begin(), A.end());
+      for (int64_t m : A) load(m, keep, order, st);
+      pairs_among(A, A, true, st);
+      v.steps.push_back(st);
+    }
+    for (size_t k = 0; k < rest.size(); k += g) {
+      std::vector<int64_t> G(rest.begin() + k, rest.begin() + std::min(rest.size(), k + g));
+      OocStep st;
+      std::set<int64_t> keep(A.begin(), A.end());
+      keep.insert(G.begin(), G.end());
+      std::vector<int64_t> later(rest.begin() + k, rest.end());
+      for (int64_t m : G) load(m, keep, later, st);
+      pairs_among(A, G, false, st);     // pairs among `rest` are left to the next phase
+      v.steps.push_back(st);
+    }
+    undone = rest;
+  }
+}
+
+// Expand each step's macro pairs into split-K tile units.
+static void build_units(VecStore &v, std::vector<int32_t> &units, std::vector<int32_t> &cover) {
+  const int64_t nch = v.Dp / kOocChunkCols;
+  for (OocStep &st : v.steps) {
+    std::vector<std::array<int32_t, 5>> tiles;   // rb_a, rb_b, ib, jb
+    for (const OocPair &pp : st.pairs) {
+      for (int h = 0; h < 2; ++h) {
+        const int64_t ib = 2LL * pp.a + h, i0 = ib * kRowBlock;
+        const int64_t jmax = std::min<int64_t>((int64_t)pp.b * kMacro + kMacro, v.n) - 1;
+        if (i0 >= v.n || i0 >= jmax) continue;
+        tiles.push_back({2 * pp.slot_a + h, 2 * pp.slot_b, (int32_t)ib, pp.b, 0});
+      }
+    }
+    const int64_t T = (int64_t)tiles.size();
+    int64_t ks = T > 0 ? (2LL * num_sms() + T - 1) / T : 1;
+    ks = std::max<int64_t>(1, std::min<int64_t>(ks, std::min<int64_t>(32, nch)));
+    st.unit0 = (int64_t)units.size() / kOocTileInts;
+    st.cover0 = (int64_t)cover.size() / kOocTileInts;
+    for (const auto &t : tiles) {
+      for (int64_t k = 0; k < ks; ++k) {
+        const int32_t c0 = (int32_t)(k * nch / ks), c1 = (int32_t)((k + 1) * nch / ks);
+        const int32_t u[kOocTileInts] = {t[0], t[1], t[1] + 1, t[2], t[3], c0, c1, 0};
+        units.insert(units.end(), u, u + kOocTileInts);
+        if (k == 0) {
+          const int32_t cu[kOocTileInts] = {t[0], t[1], t[1] + 1, t[2], t[3], 0, 0, 0};
+          cover.insert(cover.end(), cu, cu + kOocTileInts);
+        }
+      }
+    }
+    st.n_units = (int64_t)units.size() / kOocTileInts - st.unit0;
+    st.n_cover = (int64_t)cover.size() / kOocTileInts - st.cover0;
+  }
+}
+
+ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
+  VecStore &v = it->vec;
+  if (!d->data_on_host) return AP_ERR_INVALID_ARG;
+  if (v.precisions != (1u << AP_PREC_SPLIT_BF16)) return AP_ERR_UNSUPPORTED;
+  v.out_of_core = true;
+  v.h_src = d->data;
+  v.slot_cache_bytes = d->slot_cache_bytes;
+  v.n_macros = (v.n + kMacro - 1) / kMacro;
+  const uint64_t slot_bytes = (uint64_t)kMacro * v.Dp * 2 * sizeof(__nv_bfloat16);
+  v.n_slots = (int64_t)std::min<uint64_t>(d->slot_cache_bytes / slot_bytes, (uint64_t)v.n_macros);
+  if (v.n_slots < 3 && v.n_slots < v.n_macros) return AP_ERR_INVALID_ARG;   // cache too small
+  v.group = std::max<int64_t>(1, std::min<int64_t>(4, v.n_slots / 4));
+  v.ring = std::max<int64_t>(2, v.group);
+  const int64_t pool_rows = 2 * kRowBlock * v.n_slots;
+  AP_TRY(dmalloc(&v.d_pool_hi, (size_t)pool_rows * v.Dp));
+  AP_TRY(dmalloc(&v.d_pool_lo, (size_t)pool_rows * v.Dp));
+  AP_TRY(cudaMemset(v.d_pool_hi, 0, (size_t)pool_rows * v.Dp * 2));
+  AP_TRY(cudaMemset(v.d_pool_lo, 0, (size_t)pool_rows * v.Dp * 2));
+  AP_TRY(dmalloc(&v.d_raw, (size_t)v.ring * kMacro * v.ld));
+  AP_TRY(make_tc_tensor_maps(v.d_pool_hi, v.d_pool_lo, pool_rows, v.Dp, &v.tmap_pool_hi,
+                             &v.tmap_pool_lo));
+  for (int64_t b = 0; b < v.ring; ++b) {
+    cudaEvent_t a, f;
+    AP_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    v.ev_raw_ready.push_back(a);
+    AP_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+    v.ev_raw_free.push_back(f);
+  }
+  v.ring_used.assign(v.ring, 0);
+  build_schedule(v);
+  std::vector<int32_t> units, cover;
+  build_units(v, units, cover);
+  AP_TRY(dmalloc(&v.d_units, std::max<size_t>(units.size(), kOocTileInts)));
+  AP_TRY(dmalloc(&v.d_cover_units, std::max<size_t>(cover.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(v.d_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  if (!cover.empty())
+    AP_TRY(cudaMemcpy(v.d_cover_units, cover.data(), cover.size() * 4, cudaMemcpyHostToDevice));
+  AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(num_sms())));
+  v.ooc_loads = 0;
+  v.ooc_uses = 0;
+  for (const OocStep &st : v.steps) {
+    v.ooc_loads += (int64_t)st.loads.size();
+    std::set<int32_t> used;
+    for (const OocPair &pp : st.pairs) { used.insert(pp.a); used.insert(pp.b); }
+    v.ooc_uses += (int64_t)used.size();
+  }
+  return AP_OK;
+}
+
+ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s) {
+  VecStore &v = it->vec;
+  const int64_t P = v.n * (v.n - 1) / 2;
+  if (!coverage) AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
+  // copies must follow whatever the caller queued before this call
+  AP_TRY(cudaEventRecord(it->ev_a, s));
+  AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
+  uint64_t h2d = 0;
+  int64_t item_loads = 0;
+  int64_t ring_pos = 0;
+  for (const OocStep &st : v.steps) {
+    if (!coverage) {
+      for (const auto &ld : st.loads) {
+        const int64_t m = ld.first, slot = ld.second;
+        const int64_t b = ring_pos++ % v.ring;
+        const int64_t r0 = m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
+        float *raw = v.d_raw + (size_t)b * kMacro * v.ld;
+        if (v.ring_used[b]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[b], 0));
+        AP_TRY(cudaMemcpyAsync(raw, v.h_src + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
+                               cudaMemcpyHostToDevice, it->copy_stream));
+        AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
+        AP_TRY(cudaStreamWaitEvent(s, v.ev_raw_ready[b], 0));
+        AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, s));
+        const size_t slot_off = (size_t)slot * kMacro * v.Dp;
+        AP_TRY(launch_vec_split(raw, r0, 0, rows, v.D, v.ld, v.Dp, v.d_mu, v.d_pool_hi + slot_off,
+                                v.d_pool_lo + slot_off, nullptr, v.d_part, v.d_ss, v.d_rs, s));
+        AP_TRY(cudaEventRecord(v.ev_raw_free[b], s));
+        v.ring_used[b] = 1;
+        h2d += (uint64_t)rows * v.ld * 4;
+        item_loads += rows;
+      }
+    }
+    const int32_t *units = coverage ? v.d_cover_units + st.cover0 * kOocTileInts
+                                    : v.d_units + st.unit0 * kOocTileInts;
+    const int64_t nu = coverage ? st.n_cover : st.n_units;
+    AP_TRY(launch_gram_tc(v.tmap_pool_hi, v.tmap_pool_lo, v.n, v.Dp, v.d_rs, units, nu,
+                          it->d_queue, it->d_status, v.d_g64, out, coverage, 1, s));
+  }
+  if (!coverage && v.n > 1) {
+    const int grid = (int)std::min<int64_t>(v.n - 1, 65535);
+    ooc_finalize_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<double *>(out), v.d_rs, v.n);
+    AP_TRY(cudaGetLastError());
+  }
+  it->stats.tiles = 0;
+  for (const OocStep &st : v.steps) it->stats.tiles += coverage ? st.n_cover : st.n_units;
+  it->stats.tile_m = kTcTileM;
+  it->stats.tile_n = kTcTileN;
+  it->stats.item_loads = coverage ? 0 : item_loads;
+  it->stats.reuse_R = coverage ? 0.0 : (double)item_loads / (double)v.n;
+  it->stats.h2d_bytes = h2d;
+  it->stats.slot_hit_rate =
+      v.ooc_uses > 0 ? 1.0 - (double)v.ooc_loads / (double)v.ooc_uses : 1.0;
+  return AP_OK;
+}
+
+}  // namespace ap
+
+using namespace ap;
+
+extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
+                                         int64_t *n_slots, int64_t *n_loads, int64_t *n_steps) {
+  if (n_items < 0 || dim < 2 || !n_slots || !n_loads || !n_steps) return AP_ERR_INVALID_ARG;
+  VecStore v;
+  v.n = n_items;
+  v.D = dim;
+  v.Dp = (dim + 63) / 64 * 64;
+  v.n_macros = (n_items + 255) / 256;
+  const uint64_t slot_bytes = 256ull * v.Dp * 4;
+  v.n_slots = (int64_t)std::min<uint64_t>(slot_cache_bytes / slot_bytes, (uint64_t)v.n_macros);
+  if (v.n_slots < 3 && v.n_slots < v.n_macros) return AP_ERR_INVALID_ARG;
+  v.group = std::max<int64_t>(1, std::min<int64_t>(4, v.n_slots / 4));
+  build_schedule(v);
+  // every macro pair (a <= b) exactly once, both macros resident in the slots named
+  std::vector<int32_t> seen((size_t)v.n_macros * v.n_macros, 0);
+  std::vector<int64_t> holder(v.n_slots, -1);
+  int64_t loads = 0;
+  for (const OocStep &st : v.steps) {
+    for (const auto &ld : st.loads) { holder[ld.second] = ld.first; ++loads; }
+    for (const OocPair &pp : st.pairs) {
+      if (pp.a > pp.b || holder[pp.slot_a] != pp.a || holder[pp.slot_b] != pp.b) return AP_ERR_STATE;
+      seen[(size_t)pp.a * v.n_macros + pp.b] += 1;
+    }
+  }
+  for (int64_t a = 0; a < v.n_macros; ++a)
+    for (int64_t b = a; b < v.n_macros; ++b)
+      if (seen[(size_t)a * v.n_macros + b] != 1) return AP_ERR_STATE;
+  *n_slots = v.n_slots;
+  *n_loads = loads;
+  *n_steps = (int64_t)v.steps.size();
+  return AP_OK;
+}

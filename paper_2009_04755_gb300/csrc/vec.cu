@@ -80,15 +80,16 @@ vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
 // Grid: x = kSplitParts column ranges of a row, y = rows (strided).
 template <bool VEC4>
 __global__ void __launch_bounds__(kSplitThreads)
-vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t n, int64_t D, int64_t ld,
-                 int64_t Dp, const double *__restrict__ mu, __nv_bfloat16 *__restrict__ hi,
-                 __nv_bfloat16 *__restrict__ lo, float *__restrict__ c32,
-                 double *__restrict__ part) {
+vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, int64_t n,
+                 int64_t D, int64_t ld, int64_t Dp, const double *__restrict__ mu,
+                 __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                 float *__restrict__ c32, double *__restrict__ part) {
   __shared__ double red[33];
   const int64_t q4 = Dp >> 2;                  // float4 groups per padded row
   const int64_t nkb_tc = Dp / kTcKBlock, nkb_32 = Dp / kF32KBlock;
   for (int64_t lr = blockIdx.y; lr < n; lr += gridDim.y) {
-    const int64_t row = row0 + lr;             // global item index
+    const int64_t row = row0 + lr;             // global item index (statistics)
+    const int64_t orow = out_row0 + lr;        // row of the blocked copies
     const float *x = X + lr * ld;
     const double m = mu[row];
     const float mh = (float)m;
@@ -122,12 +123,12 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t n, int64_t D
         hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
         lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
         lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
-        const size_t o = blocked_offset(row, k, nkb_tc, kTcKBlock);
+        const size_t o = blocked_offset(orow, k, nkb_tc, kTcKBlock);
         *reinterpret_cast<uint2 *>(hi + o) = hv;
         *reinterpret_cast<uint2 *>(lo + o) = lv;
       }
       if (c32) {
-        const size_t o = blocked_offset(row, k, nkb_32, kF32KBlock);
+        const size_t o = blocked_offset(orow, k, nkb_32, kF32KBlock);
         *reinterpret_cast<float4 *>(c32 + o) = make_float4(c[0], c[1], c[2], c[3]);
       }
       // fold every 16 float4 (64 elements) into FP64
@@ -266,17 +267,17 @@ cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t n, int64_t D, int64_t ld,
+cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D, int64_t ld,
                              int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                              float *c32, double *part, double *ss, double *rs, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
   const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   if (vec4)
-    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(X, row0, n, D, ld, Dp, mu, hi, lo, c32,
+    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32,
                                                           part);
   else
-    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(X, row0, n, D, ld, Dp, mu, hi, lo,
+    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(X, row0, out_row0, n, D, ld, Dp, mu, hi, lo,
                                                            c32, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -114,3 +114,28 @@ def test_desc_layout_matches_header(ap):
     assert ctypes.sizeof(ap.ItemsDesc) == 104
     assert ap.ItemsDesc.slot_cache_bytes.offset == 96
     assert ctypes.sizeof(ap.RunStats) == 56
+
+
+@pytest.mark.parametrize("n,dim,slots", [(1000, 3000, 3), (4096, 65536, 6), (8192, 3 << 20, 16),
+                                         (16384, 3 << 20, 32), (5000, 100, 7), (300, 64, 50)])
+def test_out_of_core_schedule_covers_every_macro_pair(ap, n, dim, slots):
+    # the library verifies the schedule itself (each macro pair once, both
+    # macros resident); here: loads are at least one per macro, exactly one
+    # when everything fits, and every loaded byte is a macro of the set
+    dp = (dim + 63) // 64 * 64
+    cache = slots * 256 * dp * 4
+    r = ap.plan_out_of_core(n, dim, cache)
+    macros = (n + 255) // 256
+    assert r["macros"] == macros
+    assert r["slots"] == min(slots, macros)
+    assert r["loads"] >= macros
+    if slots >= macros:
+        assert r["loads"] == macros and r["steps"] == 1
+    else:
+        assert r["loads"] / macros < 2.5
+
+
+def test_out_of_core_schedule_rejects_tiny_cache(ap):
+    with pytest.raises(ap.APError) as e:
+        ap.plan_out_of_core(4096, 1024, 2 * 256 * 1024 * 4)
+    assert e.value.status == ap.AP_ERR_INVALID_ARG

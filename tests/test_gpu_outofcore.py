@@ -1,0 +1,103 @@
+"""GPU parity of the out-of-core Pearson path: vectors stay in page-locked
+host memory and stream through the HBM slot cache (the device cache of
+Sec. IV-A), checked against the FP64 oracle and the in-HBM path."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import PEARSON_ATOL, pearson_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ap():
+    import paper_2009_04755_gb300 as ap
+    ap.lib()
+    return ap
+
+
+def _slot_bytes(D):
+    return 256 * ((D + 63) // 64 * 64) * 4
+
+
+@pytest.mark.parametrize("n,D,slots", [(1000, 3000, 3), (1100, 2048, 3), (513, 1000, 9)])
+def test_out_of_core_all_pairs(ap, oracle_lib, n, D, slots):
+    X = synth.vectors_grouped(n, D, seed=n).pin_memory()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    with ap.Items.from_vectors(X, slot_cache_bytes=slots * _slot_bytes(D)) as it:
+        got = it.run_pairs().cpu().numpy()
+        st = it.stats()
+        again = it.run_pairs().cpu().numpy()
+        assert it.last_device_error() == 0
+    tol = pearson_tolerance(X.numpy(), pi, pj, 1)
+    assert np.all(np.abs(got - ref) <= tol), float(np.abs(got - ref).max())
+    np.testing.assert_allclose(again, got, rtol=0, atol=1e-12)
+    macros = (n + 255) // 256
+    plan = ap.binding.plan_out_of_core(n, D, slots * _slot_bytes(D))
+    assert st["reuse_R"] >= 1.0
+    assert st["item_loads"] >= n
+    if slots >= macros:
+        assert st["item_loads"] == n
+    assert st["h2d_bytes"] == st["item_loads"] * D * 4
+    assert plan["loads"] >= macros
+
+
+def test_out_of_core_matches_in_hbm_path(ap):
+    n, D = 900, 4096
+    X = synth.vectors_grouped(n, D, seed=3)
+    with ap.Items.from_vectors(X.cuda()) as it:
+        r_hbm = it.run_pairs().cpu().numpy()
+    with ap.Items.from_vectors(X.pin_memory(), slot_cache_bytes=3 * _slot_bytes(D) + 1) as it:
+        r_ooc = it.run_pairs().cpu().numpy()
+    # same products; only the grouping of the FP32 chunk sums differs (K is
+    # split into ranges whose sums meet in FP64): ~2^-24 sqrt(chunks) relative
+    assert np.abs(r_hbm - r_ooc).max() <= 1e-7
+
+
+def test_out_of_core_coverage(ap):
+    n, D = 1300, 64
+    X = synth.vectors_grouped(n, D, seed=5).pin_memory()
+    with ap.Items.from_vectors(X, slot_cache_bytes=3 * _slot_bytes(D)) as it:
+        cnt = it.run_pairs(ap.AP_FN_COVERAGE).cpu().numpy()
+    assert cnt.shape == (n * (n - 1) // 2,)
+    assert np.all(cnt == 1)
+
+
+def test_out_of_core_rejects(ap):
+    X = torch.randn(600, 128)
+    with pytest.raises(ap.APError):           # device data cannot be out of core
+        ap.Items.from_vectors(X.cuda(), slot_cache_bytes=1 << 30)
+    with pytest.raises(ap.APError):           # fewer than 3 slots for 3 macros
+        ap.Items.from_vectors(X.pin_memory(), slot_cache_bytes=_slot_bytes(128))
+    with ap.Items.from_vectors(X.pin_memory(), slot_cache_bytes=3 * _slot_bytes(128)) as it:
+        with pytest.raises(ap.APError):       # storage is not resident
+            it.update(X.cuda())
+        with pytest.raises(ap.APError):       # FP32 path is not built out of core
+            it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32)
+
+
+def test_out_of_core_larger_sampled(ap, oracle_lib):
+    n, D = 4096, 65536
+    X = synth.vectors_grouped(n, D, seed=11).pin_memory()
+    with ap.Items.from_vectors(X, slot_cache_bytes=6 * _slot_bytes(D)) as it:
+        r = it.run_pairs()
+        torch.cuda.synchronize()
+        st = it.stats()
+    rng = np.random.default_rng(2)
+    pi = rng.integers(0, n - 1, 3000)
+    pj = rng.integers(0, n, 3000)
+    keep = pi < pj
+    pi, pj = pi[keep], pj[keep]
+    rows = np.unique(np.concatenate([pi, pj]))
+    sub = X.numpy()[rows]
+    remap = {v: k for k, v in enumerate(rows)}
+    a = np.array([remap[v] for v in pi]); b = np.array([remap[v] for v in pj])
+    ref = oracle_lib.pearson(sub, a, b)
+    p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+    got = r[p].cpu().numpy()
+    assert np.all(np.abs(got - ref) <= pearson_tolerance(sub, a, b, 1))
+    assert 1.0 < st["reuse_R"] < 2.5
