@@ -29,9 +29,10 @@ METRIC = "pair evals/s + % of roofline; split-BF16 vs FP32 speedup at ≤1e-6 er
 N_ITEMS, DIM = 8192, 1 << 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram launch; see
-# profiles/ (None until a capture of the current kernel exists)
-GRAM_TRAFFIC_BYTES = None
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram launch at
+# 8192 x 2^20, captured at full size (a one-pass metric set) on the kernel
+# as it stands; None whenever the kernel has changed since the capture
+GRAM_TRAFFIC_BYTES = 723495411968 + 18084992000
 
 
 def peaks():
@@ -185,7 +186,7 @@ def ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    n, D = N_ITEMS, DIM
+    n, D = args.n or N_ITEMS, args.dim or DIM
     P = n * (n - 1) // 2
     stream = torch.cuda.current_stream()
     X = synth.vectors_grouped(n, D, seed=0, device="cuda")
@@ -236,7 +237,7 @@ def ours(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
-            "config": {"workload": "pearson_n8192_d1048576", "n_items": n, "dim": D,
+            "config": {"workload": f"pearson_n{n}_d{D}", "n_items": n, "dim": D,
                        "pairs": P, "precision": "split-bf16",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (32 GiB raw + 32 GiB hi/lo) far larger than L2"},
@@ -412,7 +413,7 @@ def run_cloud_workload(args):
     if wl == "overlap2d_n256":
         c = synth.clouds_uniform(n=256, dim=2, size=(64, 128), seed=0)
     elif wl == "overlap3d_n20000":
-        c = synth.clouds_lognormal(n=20000, dim=3, seed=0)
+        c = synth.clouds_lognormal(n=args.n or 20000, dim=3, seed=0)
     else:
         c = synth.clouds_templates(n=1024, seed=0)
     n = len(c["offsets"]) - 1
@@ -420,7 +421,12 @@ def run_cloud_workload(args):
     sizes = np.diff(c["offsets"]).astype(np.float64)
     point_pairs = (sizes.sum() ** 2 - (sizes ** 2).sum()) / 2
     items = ap.Items.from_clouds(c)
-    tuned = items.tune(1 if wl == "register2d_n1024" else 0)
+    if args.plan:
+        bi, bp, rr = (int(v) for v in args.plan.split(","))
+        items.set_plan(bi, bp, rr)
+        tuned = items.plan()
+    else:
+        tuned = items.tune(1 if wl == "register2d_n1024" else 0)
     stream = torch.cuda.current_stream()
     out = torch.empty(P, dtype=torch.float32, device="cuda")
     n_asc = 20
@@ -458,7 +464,8 @@ def run_cloud_workload(args):
             "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": wl, "n_items": n, "pairs": P, "point_pairs": point_pairs,
+            "config": {"workload": f"overlap3d_n{n}" if wl == "overlap3d_n20000" else wl,
+                       "n_items": n, "pairs": P, "point_pairs": point_pairs,
                        "plan": tuned},
             "point_pairs_per_s": point_pairs * (n_asc if wl == "register2d_n1024" else 1)
             / (ms / 1e3),
@@ -503,6 +510,11 @@ def main():
                     choices=["pearson_n8192_d1048576", "overlap2d_n256", "overlap3d_n20000",
                              "register2d_n1024", "pearson_ooc_n8192_d3145728"])
     ap.add_argument("--ref-pairs", type=int, default=2000)
+    ap.add_argument("--n", type=int, default=0,
+                    help="item count override (smaller cases for profiling)")
+    ap.add_argument("--dim", type=int, default=0, help="vector length override")
+    ap.add_argument("--plan", default="",
+                    help="cloud tile plan block_items,block_pts,reg_r instead of tuning")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
