@@ -203,6 +203,42 @@ ap_status ap_destroy(ap_items *items);
 /* Statistics of the last ap_run_pairs (host struct, caller-owned). */
 ap_status ap_get_stats(const ap_items *items, ap_run_stats *out);
 
+/*
+ * ap_tune -- autotune the tile plan of a point-cloud set: the block size of
+ * the recursively ordered upper triangle (Sec. IV-B) and the register
+ * blocking.  Every candidate (block_items in {2, 4, 8, 16, 32}, block_pts in
+ * {2048, 4096, 8192}, reg_r in {2, 4}) is timed on an even sample of its own
+ * tiles (~2e10 point pairs, or all of them) and the fastest becomes the
+ * handle's plan.  mode 0 tunes the overlap cost, mode 1 the adjoint / ascent
+ * kernel (2-D only).  Synchronises `stream`; allocates temporary device
+ * memory.  *out (may be NULL) receives the plan and its measured rate.
+ * Errors: AP_ERR_INVALID_ARG, AP_ERR_UNSUPPORTED (vector sets), AP_ERR_CUDA.
+ */
+ap_status ap_tune(ap_items *items, int32_t mode, void *stream, ap_plan *out);
+
+/* Current plan of a handle (vector sets report their fixed 128 x 256 tile). */
+ap_status ap_get_plan(const ap_items *items, ap_plan *out);
+
+/* Install a plan, e.g. a cached tuning result; `sorted` and `rate` are
+ * ignored.  Synchronises the device.  Errors: AP_ERR_INVALID_ARG
+ * (block_items outside 1..32, block_pts outside 64..8192, reg_r not 2 or 4
+ * or too small for the largest item: 32 * reg_r * 128 points per item at
+ * most), AP_ERR_UNSUPPORTED (vector sets). */
+ap_status ap_set_plan(ap_items *items, const ap_plan *plan);
+
+/*
+ * ap_plan_out_of_core -- host-only preview of the out-of-core schedule for n
+ * vectors of length dim and a slot cache of slot_cache_bytes (the device cache
+ * of Sec. IV-A, here holding pre-processed 256-item macros of 256*Dp*4 bytes,
+ * Dp = dim rounded up to 64).  Builds the schedule, checks that every macro
+ * pair is computed exactly once with both macros resident, and reports the
+ * slots, the macro loads (R = loads / ceil(n/256), Sec. VI-A) and the steps.
+ * Errors: AP_ERR_INVALID_ARG (bad sizes, NULL outputs, fewer than 3 slots
+ * while the set does not fit), AP_ERR_STATE (schedule check failed).
+ */
+ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
+                              int64_t *n_slots, int64_t *n_loads, int64_t *n_steps);
+
 /* Static, NUL-terminated description of a status code. */
 const char *ap_status_string(ap_status s);
 

@@ -6,9 +6,11 @@
 //   f(i,j) = sum_a sum_b w_a w_b exp(-|x_a - (R x_b + t)|^2 / (2 (s_a^2 + s_b^2)))
 //
 // Storage (built by cloud_pack): items in planner order, padded to multiples
-// of 4 points, s2k = 2 ln2 sigma^2 and lw = log2 w, so each term is
+// of 4 points, s2k = 2 ln2 sigma^2 (stored negated) and lw = log2 w, so each
+// term is
 //   w_a * 2^(lw_b - d^2 / (s2k_a + s2k_b))
-// = one add, one MUFU reciprocal, one FMA and one MUFU ex2 after d^2.
+// = one add, one MUFU reciprocal, one FMA and one MUFU ex2 after d^2; the
+// FP32 work runs as packed FP32x2 operations on two a-points at a time.
 // With a transform the a-points are moved instead of the b-points:
 //   |x_a - (R x_b + t)| = |R^T (x_a - t) - x_b|,
 // so the inner loop is unchanged, and the adjoint follows from
@@ -199,26 +201,38 @@ overlap_kernel(Params P) {
         const int i = c.i_begin + il;
         const int64_t a_begin = P.poff[i] + (int64_t)s_rj_chunk[rj] * CH;
         const int64_t a_end = P.poff[i] + P.cnt[i];
-        // this lane's a-points (padding and out-of-chunk points get weight 0)
-        float ax[R], ay[R], az[R], as[R], aw[R];
+        // this lane's a-points, two per float2 (packed FP32x2 arithmetic);
+        // coordinates kept negated so d = b - a is one add, s2k is stored
+        // negated; padding and out-of-chunk points get weight 0
+        constexpr int R2 = R / 2;
+        float2 nax[R2], nay[R2], naz[R2], nas[R2], aw2[R2];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int64_t a = a_begin + r * 32 + lane;
-          if (a < a_end) {
-            float4 p = __ldg(P.pts + a);
-            ax[r] = p.x; ay[r] = p.y;
-            if (DIM == 3) { az[r] = p.z; as[r] = p.w; aw[r] = HAS_W ? exp2f(__ldg(P.lw + a)) : 1.f; }
-            else { az[r] = 0.f; as[r] = p.z; aw[r] = exp2f(p.w); }
-          } else {
-            ax[r] = 0.f; ay[r] = 0.f; az[r] = 0.f; as[r] = 1.f; aw[r] = 0.f;
+        for (int p = 0; p < R2; ++p) {
+          float v[2][5];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int64_t a = a_begin + (2 * p + h) * 32 + lane;
+            if (a < a_end) {
+              const float4 q = __ldg(P.pts + a);
+              v[h][0] = q.x; v[h][1] = q.y;
+              if (DIM == 3) { v[h][2] = q.z; v[h][3] = q.w; v[h][4] = HAS_W ? exp2f(__ldg(P.lw + a)) : 1.f; }
+              else { v[h][2] = 0.f; v[h][3] = q.z; v[h][4] = exp2f(q.w); }
+            } else {
+              v[h][0] = 0.f; v[h][1] = 0.f; v[h][2] = 0.f; v[h][3] = -1.f; v[h][4] = 0.f;
+            }
           }
+          nax[p] = make_float2(-v[0][0], -v[1][0]);
+          nay[p] = make_float2(-v[0][1], -v[1][1]);
+          naz[p] = make_float2(-v[0][2], -v[1][2]);
+          nas[p] = make_float2(v[0][3], v[1][3]);
+          aw2[p] = make_float2(v[0][4], v[1][4]);
         }
         const int j_first = diag ? (il + 1) : 0;
         for (int jl = j_first; jl < nJ; ++jl) {
           const int j = c.j_begin + jl;
           const int b0 = (int)(P.poff[j] - c.j_pt0), b1 = b0 + P.cnt[j];
-          // transformed a-points for this pair: a' = R^T (x_a - t)
-          float tx_[R], ty_[R];
+          // -a' = R^T (-(x_a - t)) for this pair's transform
+          float2 ntx[R2], nty[R2];
           float cth = 1.f, sth = 0.f, ttx = 0.f, tty = 0.f;
           int64_t pidx = 0;
           if (MODE == FWD_T || MODE == GRAD) {
@@ -232,64 +246,83 @@ overlap_kernel(Params P) {
             }
           }
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
+          for (int p = 0; p < R2; ++p) {
             if (MODE == FWD_T || MODE == GRAD) {
-              const float ux = ax[r] - ttx, uy = ay[r] - tty;
-              tx_[r] = cth * ux + sth * uy;
-              ty_[r] = -sth * ux + cth * uy;
+              const float2 ux = __fadd2_rn(nax[p], make_float2(ttx, ttx));
+              const float2 uy = __fadd2_rn(nay[p], make_float2(tty, tty));
+              ntx[p] = __ffma2_rn(make_float2(cth, cth), ux, __fmul2_rn(make_float2(sth, sth), uy));
+              nty[p] = __ffma2_rn(make_float2(cth, cth), uy, __fmul2_rn(make_float2(-sth, -sth), ux));
             } else {
-              tx_[r] = ax[r]; ty_[r] = ay[r];
+              ntx[p] = nax[p]; nty[p] = nay[p];
             }
           }
-          float accF[R], cmpF[R], accX[R], accY[R], accT[R];
+          const float2 z2 = make_float2(0.f, 0.f);
+          float2 accF[R2], cmpF[R2], accX[R2], accY[R2], accT[R2];
 #pragma unroll
-          for (int r = 0; r < R; ++r) { accF[r] = 0.f; cmpF[r] = 0.f; accX[r] = 0.f; accY[r] = 0.f; accT[r] = 0.f; }
+          for (int p = 0; p < R2; ++p) { accF[p] = z2; cmpF[p] = z2; accX[p] = z2; accY[p] = z2; accT[p] = z2; }
           for (int bb0 = b0; bb0 < b1; bb0 += 32) {
             const int bb1 = min(bb0 + 32, b1);
-            float blF[R], blX[R], blY[R], blT[R];
+            float2 blF[R2], blX[R2], blY[R2], blT[R2];
 #pragma unroll
-            for (int r = 0; r < R; ++r) { blF[r] = 0.f; blX[r] = 0.f; blY[r] = 0.f; blT[r] = 0.f; }
+            for (int p = 0; p < R2; ++p) { blF[p] = z2; blX[p] = z2; blY[p] = z2; blT[p] = z2; }
 #pragma unroll 4
             for (int b = bb0; b < bb1; ++b) {
               const float4 q = bsrc[b];
               float lwb, s2b;
               if (DIM == 3) { s2b = q.w; lwb = HAS_W ? lsrc[b] : 0.f; }
               else { s2b = q.z; lwb = q.w; }
+              const float2 bx2 = make_float2(q.x, q.x), by2 = make_float2(q.y, q.y);
+              const float2 bs2 = make_float2(s2b, s2b), lw2 = make_float2(lwb, lwb);
 #pragma unroll
-              for (int r = 0; r < R; ++r) {
-                const float dx = tx_[r] - q.x, dy = ty_[r] - q.y;
-                float d2 = dx * dx;
-                d2 = fmaf(dy, dy, d2);
-                if (DIM == 3) { const float dz = az[r] - q.z; d2 = fmaf(dz, dz, d2); }
-                const float rr = rcp_approx(as[r] + s2b);
-                const float e = ex2_approx(fmaf(-d2, rr, lwb));
-                blF[r] += e;
+              for (int p = 0; p < R2; ++p) {
+                const float2 dx = __fadd2_rn(bx2, ntx[p]);          // b - a'
+                const float2 dy = __fadd2_rn(by2, nty[p]);
+                float2 d2 = __fmul2_rn(dx, dx);
+                d2 = __ffma2_rn(dy, dy, d2);
+                if (DIM == 3) {
+                  const float2 dz = __fadd2_rn(make_float2(q.z, q.z), naz[p]);
+                  d2 = __ffma2_rn(dz, dz, d2);
+                }
+                const float2 ns = __fadd2_rn(nas[p], bs2);           // -(s2k_a + s2k_b)
+                const float2 nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                const float2 arg = __ffma2_rn(d2, nr, lw2);          // lw_b - d^2 / s2k
+                const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                blF[p] = __fadd2_rn(blF[p], e);
                 if (MODE == GRAD) {
-                  const float er = e * rr;
-                  blX[r] = fmaf(er, dx, blX[r]);
-                  blY[r] = fmaf(er, dy, blY[r]);
-                  blT[r] = fmaf(er, fmaf(q.x, dy, -q.y * dx), blT[r]);
+                  // with d' = a' - b = -(dx, dy) and -e r = e * nr:
+                  // sum e r d' = sum (e nr) (dx, dy);
+                  // sum e r (x_b d'_y - y_b d'_x) = sum (e nr) (x_b dy - y_b dx)
+                  const float2 ner = __fmul2_rn(e, nr);
+                  blX[p] = __ffma2_rn(ner, dx, blX[p]);
+                  blY[p] = __ffma2_rn(ner, dy, blY[p]);
+                  const float2 cr = __ffma2_rn(bx2, dy, __fmul2_rn(make_float2(-q.y, -q.y), dx));
+                  blT[p] = __ffma2_rn(ner, cr, blT[p]);
                 }
               }
             }
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int p = 0; p < R2; ++p) {
               // compensated add of the block sum
-              const float yk = blF[r] - cmpF[r];
-              const float tk = accF[r] + yk;
-              cmpF[r] = (tk - accF[r]) - yk;
-              accF[r] = tk;
-              if (MODE == GRAD) { accX[r] += blX[r]; accY[r] += blY[r]; accT[r] += blT[r]; }
+              const float2 yk = __fadd2_rn(blF[p], make_float2(-cmpF[p].x, -cmpF[p].y));
+              const float2 tk = __fadd2_rn(accF[p], yk);
+              const float2 dd = __fadd2_rn(tk, make_float2(-accF[p].x, -accF[p].y));
+              cmpF[p] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
+              accF[p] = tk;
+              if (MODE == GRAD) {
+                accX[p] = __fadd2_rn(accX[p], blX[p]);
+                accY[p] = __fadd2_rn(accY[p], blY[p]);
+                accT[p] = __fadd2_rn(accT[p], blT[p]);
+              }
             }
           }
           float vF = 0.f, vX = 0.f, vY = 0.f, vT = 0.f;
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            vF = fmaf(aw[r], accF[r], vF);
+          for (int p = 0; p < R2; ++p) {
+            vF = fmaf(aw2[p].x, accF[p].x, fmaf(aw2[p].y, accF[p].y, vF));
             if (MODE == GRAD) {
-              vX = fmaf(aw[r], accX[r], vX);
-              vY = fmaf(aw[r], accY[r], vY);
-              vT = fmaf(aw[r], accT[r], vT);
+              vX = fmaf(aw2[p].x, accX[p].x, fmaf(aw2[p].y, accX[p].y, vX));
+              vY = fmaf(aw2[p].x, accY[p].x, fmaf(aw2[p].y, accY[p].y, vY));
+              vT = fmaf(aw2[p].x, accT[p].x, fmaf(aw2[p].y, accT[p].y, vT));
             }
           }
 #pragma unroll
@@ -383,7 +416,7 @@ __global__ void cloud_pack_kernel(const float *__restrict__ x, const float *__re
       if (k < cnt) {
         const int64_t a = src0 + k;
         const double sg = (double)sigma[a];
-        const float s2k = (float)(two_ln2 * sg * sg);
+        const float s2k = (float)(-two_ln2 * sg * sg);   // stored negated
         const float wt = w ? w[a] : 1.f;
         l = (wt > 0.f) ? (float)log2((double)wt) : -INFINITY;
         if (dim == 3) p = make_float4(x[a], y[a], z[a], s2k);
@@ -391,8 +424,8 @@ __global__ void cloud_pack_kernel(const float *__restrict__ x, const float *__re
       } else {
         // padding (never visited: loops use the real counts), kept finite
         l = -INFINITY;
-        if (dim == 3) p = make_float4(0.f, 0.f, 0.f, 1.f);
-        else p = make_float4(0.f, 0.f, 1.f, -INFINITY);
+        if (dim == 3) p = make_float4(0.f, 0.f, 0.f, -1.f);
+        else p = make_float4(0.f, 0.f, -1.f, -INFINITY);
       }
       pts[dst0 + k] = p;
       if (lw) lw[dst0 + k] = l;
@@ -408,7 +441,6 @@ cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s)
                 (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
   void (*kern)(Params) = nullptr;
   switch (reg_r) {
-    case 1: kern = overlap_kernel<DIM, HAS_W, MODE, 1>; break;
     case 2: kern = overlap_kernel<DIM, HAS_W, MODE, 2>; break;
     default: kern = overlap_kernel<DIM, HAS_W, MODE, 4>; break;
   }

@@ -20,7 +20,7 @@ namespace ap {
 int32_t min_reg_r(const CloudStore &c) {
   int64_t mx = 0;
   for (int64_t s : c.h_size) mx = std::max(mx, s);
-  int32_t r = 1;
+  int32_t r = 2;                        // a-points go in pairs (FP32x2)
   while ((int64_t)r * 32 * kOverlapMaxRowJobs < mx && r < 4) r *= 2;
   return r;
 }
@@ -95,7 +95,7 @@ extern "C" ap_status ap_set_plan(ap_items *it, const ap_plan *plan) {
   if (it->kind == AP_ITEMS_VECTOR) return AP_ERR_UNSUPPORTED;
   if (plan->block_items < 1 || plan->block_items > kOverlapMaxBlockItems) return AP_ERR_INVALID_ARG;
   if (plan->block_pts < 64 || plan->block_pts > 8192) return AP_ERR_INVALID_ARG;
-  if (plan->reg_r != 1 && plan->reg_r != 2 && plan->reg_r != 4) return AP_ERR_INVALID_ARG;
+  if (plan->reg_r != 2 && plan->reg_r != 4) return AP_ERR_INVALID_ARG;
   if (plan->reg_r < min_reg_r(it->cl)) return AP_ERR_INVALID_ARG;
   CloudPlanChoice ch{plan->block_items, plan->block_pts, plan->reg_r, it->cl.sorted};
   cudaError_t e = cudaDeviceSynchronize();      // the old plan may still be in use
@@ -131,7 +131,7 @@ extern "C" ap_status ap_tune(ap_items *it, int32_t mode, void *stream, ap_plan *
   CloudPlanChoice best{0, 0, 0, c.sorted};
   double best_rate = -1.0;
   const int32_t rmin = min_reg_r(c);
-  for (int32_t rr : {1, 2, 4}) {
+  for (int32_t rr : {2, 4}) {
     if (rr < rmin || e != cudaSuccess) continue;
     for (int32_t bp : {2048, 4096, 8192}) {
       for (int32_t bi : {2, 4, 8, 16, 32}) {
