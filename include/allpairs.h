@@ -239,6 +239,21 @@ ap_status ap_set_plan(ap_items *items, const ap_plan *plan);
 ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
                               int64_t *n_slots, int64_t *n_loads, int64_t *n_steps);
 
+/* Failure-path switches for testing the bounded device waits. */
+typedef enum {
+  AP_DEBUG_NONE = 0,
+  /* the tensor-core Gram's producer withholds the first stage of every tile,
+   * so the consumer's wait runs out: the kernel records a device error code
+   * (read with ap_last_device_error), every role leaves, TMEM is freed and
+   * the context stays usable */
+  AP_DEBUG_WITHHOLD_STAGE = 1
+} ap_debug_flags;
+
+/* ap_set_debug -- set the failure-path switch and the wall-clock budget of
+ * every bounded device wait (nanoseconds; 0 restores the 2 s default) for
+ * the handle's later launches.  Errors: AP_ERR_INVALID_ARG (unknown flag). */
+ap_status ap_set_debug(ap_items *items, int32_t flags, uint64_t wait_budget_ns);
+
 /* Static, NUL-terminated description of a status code. */
 const char *ap_status_string(ap_status s);
 

@@ -80,6 +80,7 @@ def lib():
             "ap_plan_tiles": (i32, [i64, i32, vp, i64, ctypes.POINTER(i64)]),
             "ap_tune": (i32, [vp, i32, vp, ctypes.POINTER(Plan)]),
             "ap_get_plan": (i32, [vp, ctypes.POINTER(Plan)]),
+            "ap_set_debug": (i32, [vp, i32, ctypes.c_uint64]),
             "ap_set_plan": (i32, [vp, ctypes.POINTER(Plan)]),
             "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]),
@@ -270,6 +271,10 @@ class Items:
         st = RunStats()
         check(lib().ap_get_stats(self._h, ctypes.byref(st)), "ap_get_stats")
         return {k: getattr(st, k) for k, _ in RunStats._fields_}
+
+    def set_debug(self, flags: int, wait_budget_ns: int = 0):
+        """Failure-path switch (testing) and device wait budget (0 = 2 s)."""
+        check(lib().ap_set_debug(self._h, int(flags), int(wait_budget_ns)), "ap_set_debug")
 
     def last_device_error(self) -> int:
         return int(lib().ap_last_device_error(self._h))

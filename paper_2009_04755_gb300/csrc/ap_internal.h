@@ -147,6 +147,8 @@ struct ap_items {
   cudaStream_t graph_stream = nullptr;   // private stream the graphs are captured on
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint64_t plan_version = 0;
+  uint64_t wait_budget_ns = 0;          // 0 = the default budget
+  int32_t debug = 0;                    // failure-path testing switches
   std::vector<ap::GraphEntry> graphs;
 };
 
@@ -199,7 +201,8 @@ cudaError_t make_tc_tensor_maps(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo
 cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
                            const double *rs, const int32_t *tiles, int64_t n_tiles,
                            int32_t *queue, int32_t *status, double *g64, void *out,
-                           int coverage, int ooc, cudaStream_t s);
+                           int coverage, int ooc, uint64_t budget, int32_t debug,
+                           cudaStream_t s);
 // out-of-core unit: {A row block, B row blocks (2), I block, J block, chunk
 // begin, chunk end, unused}; chunks are 64 columns of D
 constexpr int kOocTileInts = 8;

@@ -419,7 +419,8 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
     if (!use_split && !have_f32) return AP_ERR_STATE;
     if (use_split) {
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_tiles_tc, v.n_tiles_tc,
-                            it->d_queue, it->d_status, v.d_g64, out, cover, 0, s));
+                            it->d_queue, it->d_status, v.d_g64, out, cover, 0,
+                            it->wait_budget_ns, it->debug, s));
       it->stats.tiles = v.n_tiles_tc;
       it->stats.tile_m = kTcTileM;
       it->stats.tile_n = kTcTileN;
@@ -491,6 +492,14 @@ ap_status ap_destroy(ap_items *it) {
 ap_status ap_get_stats(const ap_items *it, ap_run_stats *out) {
   if (!it || !out) return AP_ERR_INVALID_ARG;
   *out = it->stats;
+  return AP_OK;
+}
+
+ap_status ap_set_debug(ap_items *it, int32_t flags, uint64_t wait_budget_ns) {
+  if (!it) return AP_ERR_INVALID_ARG;
+  if (flags != AP_DEBUG_NONE && flags != AP_DEBUG_WITHHOLD_STAGE) return AP_ERR_INVALID_ARG;
+  it->debug = flags;
+  it->wait_budget_ns = wait_budget_ns;
   return AP_OK;
 }
 

@@ -15,7 +15,7 @@
 //               and commits each stage back to the producer;
 //   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, FP64
 //               scaling, packed upper-triangle stores.
-// Every wait is bounded (kWaitBudgetNs); when one runs out the CTA records a
+// Every wait is bounded (a per-launch budget, 2 s by default); when one runs out the CTA records a
 // device error code, drains its in-flight copies, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -80,14 +80,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // bounded wait: false when the budget ran out or another role aborted
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          volatile int *abort_flag) {
+                                          volatile int *abort_flag, uint64_t budget) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitBudgetNs) return false;
+      if (global_ns() - t0 > budget) return false;
     }
   }
 }
@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                int64_t n, int64_t Dp, const double *__restrict__ rs,
                const int32_t *__restrict__ tiles, int64_t n_tiles, int32_t *queue,
-               int32_t *status, double *__restrict__ g64, void *out) {
+               int32_t *status, double *__restrict__ g64, void *out, uint64_t budget,
+               int32_t debug) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -250,13 +251,19 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       // ---------------- TMA producer ----------------
       const int64_t kb0 = c_begin * kChunkStages;
       for (int64_t kb = kb0; kb < kb0 + nchunks * kChunkStages; ++kb) {
-        if (!mbar_wait(empty_bar(p_stage), p_phase ^ 1, s_abort)) {
+        if (!mbar_wait(empty_bar(p_stage), p_phase ^ 1, s_abort, budget)) {
           atomicCAS(status, 0, DEV_TIMEOUT_EMPTY);
           *s_abort = 1;
           break;
         }
         const uint32_t fb = full_bar(p_stage);
         const uint32_t sb = smem_base + p_stage * STAGE_BYTES;
+        // debug 1 withholds the first stage of every tile: the consumer's
+        // bounded wait must run out and report (failure-path testing only)
+        if (debug == 1 && kb == kb0) {
+          if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
+          continue;
+        }
         mbar_expect_tx(fb, STAGE_BYTES);
         const int32_t k = (int32_t)kb;
         tma_load_block(sb, &tm_hi, fb, k, rb_a);
@@ -274,7 +281,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       uint32_t mc = cc;
       for (int64_t c = 0; c < nchunks && !*s_abort; ++c, ++mc) {
         const uint32_t a = mc & 1, use = mc >> 1;
-        if (!mbar_wait(tempty_bar(a), (use & 1) ^ 1, s_abort)) {
+        if (!mbar_wait(tempty_bar(a), (use & 1) ^ 1, s_abort, budget)) {
           atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
           *s_abort = 1;
           break;
@@ -283,7 +290,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         const uint32_t dt = tmem + a * BN;
         bool ok = true;
         for (int s = 0; s < kChunkStages; ++s) {
-          if (!mbar_wait(full_bar(m_stage), m_phase, s_abort)) {
+          if (!mbar_wait(full_bar(m_stage), m_phase, s_abort, budget)) {
             atomicCAS(status, 0, DEV_TIMEOUT_FULL);
             *s_abort = 1;
             ok = false;
@@ -321,7 +328,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       uint32_t ec = cc;
       for (int64_t c = 0; c < nchunks; ++c, ++ec) {
         const uint32_t a = ec & 1, use = ec >> 1;
-        if (!mbar_wait(tfull_bar(a), use & 1, s_abort)) {
+        if (!mbar_wait(tfull_bar(a), use & 1, s_abort, budget)) {
           if (lane == 0) atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
           *s_abort = 1;
           ok = false;
@@ -384,7 +391,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       if (!issued[s]) continue;
       const uint64_t t0 = global_ns();
       while (!mbar_try_wait(full_bar(s), issued_parity[s])) {
-        if (global_ns() - t0 > kWaitBudgetNs) break;
+        if (global_ns() - t0 > budget) break;
       }
     }
   }
@@ -464,12 +471,13 @@ void free_tc_tensor_maps(void *a, void *b) {
 cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, int64_t Dp,
                            const double *rs, const int32_t *tiles, int64_t n_tiles,
                            int32_t *queue, int32_t *status, double *g64, void *out,
-                           int coverage, int ooc, cudaStream_t s) {
+                           int coverage, int ooc, uint64_t budget, int32_t debug,
+                           cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
   static bool attr_done[4] = {false, false, false, false};
   const int v = (coverage ? 1 : 0) + (ooc ? 2 : 0);
   void (*kern)(CUtensorMap, CUtensorMap, int64_t, int64_t, const double *, const int32_t *,
-               int64_t, int32_t *, int32_t *, double *, void *) =
+               int64_t, int32_t *, int32_t *, double *, void *, uint64_t, int32_t) =
       v == 0 ? gram_tc_kernel<0, 0> : v == 1 ? gram_tc_kernel<1, 0>
              : v == 2 ? gram_tc_kernel<0, 1> : gram_tc_kernel<1, 1>;
   if (!attr_done[v]) {
@@ -484,7 +492,7 @@ cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, 
   kern<<<(int)grid, NUM_THREADS, SMEM_BYTES, s>>>(
       *reinterpret_cast<const CUtensorMap *>(tmap_hi),
       *reinterpret_cast<const CUtensorMap *>(tmap_lo), n, Dp, rs, tiles, n_tiles, queue, status,
-      g64, out);
+      g64, out, budget ? budget : kWaitBudgetNs, debug);
   return cudaGetLastError();
 }
 

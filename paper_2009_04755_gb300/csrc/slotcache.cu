@@ -256,7 +256,8 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
                                     : v.d_units + st.unit0 * kOocTileInts;
     const int64_t nu = coverage ? st.n_cover : st.n_units;
     AP_TRY(launch_gram_tc(v.tmap_pool_hi, v.tmap_pool_lo, v.n, v.Dp, v.d_rs, units, nu,
-                          it->d_queue, it->d_status, v.d_g64, out, coverage, 1, s));
+                          it->d_queue, it->d_status, v.d_g64, out, coverage, 1,
+                          it->wait_budget_ns, it->debug, s));
   }
   if (!coverage && v.n > 1) {
     const int grid = (int)std::min<int64_t>(v.n - 1, 65535);
