@@ -35,7 +35,6 @@ namespace ap {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRowJobs = kOverlapMaxRowJobs;
 constexpr int kMaxBlockItems = kOverlapMaxBlockItems;
 constexpr float kTwoLn2 = 1.3862943611198906f;
@@ -109,8 +108,9 @@ overlap_kernel(Params P) {
       (reinterpret_cast<uintptr_t>(s_rj_first + kMaxBlockItems + 1) + 7) & ~uintptr_t(7));
   TileCtx *s_ctx = reinterpret_cast<TileCtx *>(s_bar + 1);
   int *s_tile = reinterpret_cast<int *>(s_ctx + 1);
+  int *s_next = s_tile + 1;                      // next (row job, partner) unit
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const uint32_t bar = smem_u32(s_bar);
   uint32_t phase = 0;
   if (threadIdx.x == 0) {
@@ -142,6 +142,7 @@ overlap_kernel(Params P) {
         }
         s_rj_first[c.i_end - c.i_begin] = (int16_t)nrj;
         c.n_rj = nrj;
+        *s_next = 0;
         c.j_pt0 = P.poff[c.j_begin];
         const int64_t jpts = P.poff[c.j_end] - c.j_pt0;
         c.use_smem = (MODE != COVER) && jpts > 0 && jpts <= P.stage_cap;
@@ -196,8 +197,16 @@ overlap_kernel(Params P) {
     if (MODE != COVER) {
       const float4 *bsrc = c.use_smem ? s_pts : (P.pts + c.j_pt0);
       const float *lsrc = c.use_smem ? s_lw : (P.lw ? P.lw + c.j_pt0 : nullptr);
-      for (int rj = warp; rj < c.n_rj; rj += kWarps) {
+      // warps take (row job, partner item) units from a shared counter, so
+      // every warp of the CTA runs until the tile's work is gone
+      for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(s_next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= c.n_rj * nJ) break;
+        const int rj = u / nJ, jl = u - rj * nJ;
         const int il = s_rj_item[rj];
+        if (diag && jl <= il) continue;
         const int i = c.i_begin + il;
         const int64_t a_begin = P.poff[i] + (int64_t)s_rj_chunk[rj] * CH;
         const int64_t a_end = P.poff[i] + P.cnt[i];
@@ -227,8 +236,7 @@ overlap_kernel(Params P) {
           nas[p] = make_float2(v[0][3], v[1][3]);
           aw2[p] = make_float2(v[0][4], v[1][4]);
         }
-        const int j_first = diag ? (il + 1) : 0;
-        for (int jl = j_first; jl < nJ; ++jl) {
+        {
           const int j = c.j_begin + jl;
           const int b0 = (int)(P.poff[j] - c.j_pt0), b1 = b0 + P.cnt[j];
           // -a' = R^T (-(x_a - t)) for this pair's transform
