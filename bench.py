@@ -289,12 +289,13 @@ def ours(args):
         Xh = synth.vectors_grouped(n, D, seed=0, device="cuda").cpu().pin_memory()
         res_h = torch.empty(P, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
-        items.update(Xh)                     # warm the host path once
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 3))
+        # the two calls in sequence: copy + pre-process, then the Gram
+        items.update(Xh)
         items.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_SPLIT_BF16, out=out)
         res_h.copy_(out, non_blocking=True)
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ksteps = max(1, min(args.steps, 3))
         e0.record(stream)
         for _ in range(ksteps):
             items.update(Xh)
@@ -302,7 +303,19 @@ def ours(args):
             res_h.copy_(out, non_blocking=True)
         e1.record(stream)
         barrier()
+        seq_ms = max_over_ranks(e0.elapsed_time(e1))
+        # the fused call: transfers overlapped with the Gram macro by macro
+        items.load_and_run(Xh, out=out)
+        res_h.copy_(out, non_blocking=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(ksteps):
+            items.load_and_run(Xh, out=out)
+            res_h.copy_(out, non_blocking=True)
+        e1.record(stream)
+        barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1))
+        line["e2e_update_then_run_ms_per_step"] = seq_ms / ksteps
         line["e2e"] = {"value": P * ws * ksteps / (e_ms / 1e3), "unit": "pairs/s",
                        "h2d_bytes_per_step": int(n * D * 4),
                        "d2h_bytes_per_step": int(P * 8), "steps": ksteps,

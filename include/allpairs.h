@@ -170,6 +170,22 @@ ap_status ap_run_pairs(ap_items *items, int32_t fn, int32_t precision,
                        const float *params, void *out, void *stream);
 
 /*
+ * ap_load_and_run -- ap_update_items from host memory fused with
+ * ap_run_pairs(AP_FN_PEARSON, AP_PREC_SPLIT_BF16) on a resident vector set:
+ * the host rows travel in 256-item macros on the library's copy stream, each
+ * macro is pre-processed as it lands, and every pair (a <= m, m) of macro m
+ * is computed right away, so the transfers overlap the Gram (the
+ * asynchronous, overlapped processing of Sec. IV-C; every item is loaded
+ * once, R = 1).  host_data: float[n_items][ld] in host memory (page-locked for
+ * the copies to overlap), read until the work on `stream` completes; out:
+ * device double[P], overwritten.  The handle's stored items become the new
+ * ones, as after ap_update_items.
+ * Errors: AP_ERR_INVALID_ARG (not a vector set, NULL pointers with P > 0),
+ * AP_ERR_STATE (out-of-core set, or no split-BF16 representation).
+ */
+ap_status ap_load_and_run(ap_items *items, const float *host_data, double *out, void *stream);
+
+/*
  * ap_backward -- adjoint of the overlap cost (2-D clouds) with respect to the
  * per-pair transform (theta, tx, ty):
  *   grad_params[p][k] = grad_out[p] * d f_p / d param_k,

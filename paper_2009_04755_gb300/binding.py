@@ -81,6 +81,7 @@ def lib():
             "ap_tune": (i32, [vp, i32, vp, ctypes.POINTER(Plan)]),
             "ap_get_plan": (i32, [vp, ctypes.POINTER(Plan)]),
             "ap_set_debug": (i32, [vp, i32, ctypes.c_uint64]),
+            "ap_load_and_run": (i32, [vp, vp, vp, vp]),
             "ap_set_plan": (i32, [vp, ctypes.POINTER(Plan)]),
             "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]),
@@ -233,6 +234,17 @@ class Items:
                 max(self.P, 1), dtype=dt, device="cuda")
         check(lib().ap_run_pairs(self._h, fn, precision, _ptr(params), _ptr(out),
                                  _stream_ptr(stream)), "ap_run_pairs")
+        return out[:self.P]
+
+    def load_and_run(self, X_host, out=None, stream=None):
+        """Load new host vectors and correlate all pairs, transfers overlapped
+        with the Gram (split-BF16)."""
+        import torch
+        assert not X_host.is_cuda and X_host.dtype == torch.float32
+        if out is None:
+            out = torch.empty(max(self.P, 1), dtype=torch.float64, device="cuda")
+        check(lib().ap_load_and_run(self._h, _ptr(X_host), _ptr(out), _stream_ptr(stream)),
+              "ap_load_and_run")
         return out[:self.P]
 
     def backward(self, params=None, grad_out=None, f_out=None, stream=None):

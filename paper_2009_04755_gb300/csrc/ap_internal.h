@@ -104,6 +104,10 @@ struct VecStore {
   int32_t *d_units = nullptr, *d_cover_units = nullptr;
   void *tmap_pool_hi = nullptr, *tmap_pool_lo = nullptr;
   int64_t ooc_loads = 0, ooc_uses = 0;
+  // streamed load-and-run of a resident set: per macro column m, the split-K
+  // units of the pairs (a <= m, m) on the resident blocked arrays
+  int32_t *d_stream_units = nullptr;
+  std::vector<std::pair<int64_t, int64_t>> stream_cols;   // (first unit, units)
   // tile plans
   int32_t *d_tiles_tc = nullptr;  int64_t n_tiles_tc = 0;
   int32_t *d_tiles_f32 = nullptr; int64_t n_tiles_f32 = 0;
@@ -269,5 +273,8 @@ void clear_graphs(ap_items *it);
 ap_status create_out_of_core(const ap_items_desc *d, ap_items *it);
 ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s);
 void free_out_of_core(VecStore &v);
+// host source streamed macro by macro into a resident set, each macro's pairs
+// computed as soon as it is pre-processed (slotcache.cu)
+ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStream_t s);
 
 }  // namespace ap

@@ -55,6 +55,8 @@ void free_out_of_core(VecStore &v) {
   dfree(v.d_raw);
   dfree(v.d_units);
   dfree(v.d_cover_units);
+  dfree(v.d_stream_units);
+  v.stream_cols.clear();
   for (cudaEvent_t e : v.ev_raw_ready) cudaEventDestroy(e);
   for (cudaEvent_t e : v.ev_raw_free) cudaEventDestroy(e);
   v.ev_raw_ready.clear();
@@ -311,4 +313,106 @@ extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t 
   *n_loads = loads;
   *n_steps = (int64_t)v.steps.size();
   return AP_OK;
+}
+
+namespace ap {
+
+// Units of the streamed run: column m holds the pairs (a <= m, m) of macros,
+// addressed directly in the resident arrays (row block = item block).
+static ap_status build_stream_units(VecStore &v) {
+  const int64_t M = (v.n + kMacro - 1) / kMacro;
+  const int64_t nch = v.Dp / kOocChunkCols;
+  std::vector<int32_t> units;
+  v.stream_cols.clear();
+  for (int64_t m = 0; m < M; ++m) {
+    std::vector<std::array<int32_t, 3>> tiles;   // ib, rb_b, jb
+    for (int64_t a = 0; a <= m; ++a)
+      for (int h = 0; h < 2; ++h) {
+        const int64_t ib = 2 * a + h, i0 = ib * kRowBlock;
+        const int64_t jmax = std::min<int64_t>(m * kMacro + kMacro, v.n) - 1;
+        if (i0 >= v.n || i0 >= jmax) continue;
+        tiles.push_back({(int32_t)ib, (int32_t)(2 * m), (int32_t)m});
+      }
+    const int64_t T = (int64_t)tiles.size();
+    int64_t ks = T > 0 ? (2LL * num_sms() + T - 1) / T : 1;
+    ks = std::max<int64_t>(1, std::min<int64_t>(ks, std::min<int64_t>(32, nch)));
+    const int64_t u0 = (int64_t)units.size() / kOocTileInts;
+    for (const auto &t : tiles)
+      for (int64_t k = 0; k < ks; ++k) {
+        const int32_t c0 = (int32_t)(k * nch / ks), c1 = (int32_t)((k + 1) * nch / ks);
+        const int32_t u[kOocTileInts] = {t[0], t[1], t[1] + 1, t[0], t[2], c0, c1, 0};
+        units.insert(units.end(), u, u + kOocTileInts);
+      }
+    v.stream_cols.push_back({u0, (int64_t)units.size() / kOocTileInts - u0});
+  }
+  AP_TRY(dmalloc(&v.d_stream_units, std::max<size_t>(units.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(v.d_stream_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  return AP_OK;
+}
+
+ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStream_t s) {
+  VecStore &v = it->vec;
+  if (!v.d_stream_units) {
+    ap_status st = build_stream_units(v);
+    if (st != AP_OK) return st;
+  }
+  if (!v.d_raw) {
+    v.ring = 2;
+    AP_TRY(dmalloc(&v.d_raw, (size_t)v.ring * kMacro * v.ld));
+    for (int64_t b = 0; b < v.ring; ++b) {
+      cudaEvent_t a, f;
+      AP_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+      v.ev_raw_ready.push_back(a);
+      AP_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+      v.ev_raw_free.push_back(f);
+    }
+    v.ring_used.assign(v.ring, 0);
+  }
+  const int64_t P = v.n * (v.n - 1) / 2;
+  AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
+  AP_TRY(cudaEventRecord(it->ev_a, s));
+  AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
+  const bool split = v.d_hi != nullptr, f32 = v.d_c32 != nullptr;
+  for (size_t m = 0; m < v.stream_cols.size(); ++m) {
+    const int64_t b = (int64_t)(m % v.ring);
+    const int64_t r0 = (int64_t)m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
+    float *raw = v.d_raw + (size_t)b * kMacro * v.ld;
+    if (v.ring_used[b]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[b], 0));
+    AP_TRY(cudaMemcpyAsync(raw, h + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
+                           cudaMemcpyHostToDevice, it->copy_stream));
+    AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
+    AP_TRY(cudaStreamWaitEvent(s, v.ev_raw_ready[b], 0));
+    AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, s));
+    AP_TRY(launch_vec_split(raw, r0, r0, rows, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
+                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
+                            v.d_rs, s));
+    AP_TRY(cudaEventRecord(v.ev_raw_free[b], s));
+    v.ring_used[b] = 1;
+    AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs,
+                          v.d_stream_units + v.stream_cols[m].first * kOocTileInts,
+                          v.stream_cols[m].second, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
+                          it->wait_budget_ns, it->debug, s));
+  }
+  if (v.n > 1) {
+    const int grid = (int)std::min<int64_t>(v.n - 1, 65535);
+    ooc_finalize_kernel<<<grid, 256, 0, s>>>(out, v.d_rs, v.n);
+    AP_TRY(cudaGetLastError());
+  }
+  it->stats.item_loads = v.n;
+  it->stats.reuse_R = 1.0;
+  it->stats.h2d_bytes = (uint64_t)v.n * v.ld * 4;
+  it->stats.slot_hit_rate = 1.0;
+  return AP_OK;
+}
+
+}  // namespace ap
+
+extern "C" ap_status ap_load_and_run(ap_items *items, const float *host_data, double *out,
+                                     void *stream) {
+  if (!items || items->kind != AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
+  if (items->vec.out_of_core || !items->vec.d_hi) return AP_ERR_STATE;
+  if (items->vec.n < 2) return AP_OK;
+  if (!host_data || !out) return AP_ERR_INVALID_ARG;
+  return stream_load_and_run(items, host_data, out, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -101,3 +101,21 @@ def test_out_of_core_larger_sampled(ap, oracle_lib):
     got = r[p].cpu().numpy()
     assert np.all(np.abs(got - ref) <= pearson_tolerance(sub, a, b, 1))
     assert 1.0 < st["reuse_R"] < 2.5
+
+
+@pytest.mark.parametrize("n,D", [(1000, 3000), (300, 200), (513, 1024)])
+def test_load_and_run_matches_separate_calls(ap, oracle_lib, n, D):
+    """Transfers overlapped with the Gram macro by macro give the same
+    correlations as loading first and running after."""
+    X1 = synth.vectors_grouped(n, D, seed=21)
+    X2 = synth.vectors_grouped(n, D, seed=22).pin_memory()
+    pi, pj = oracle_lib.all_pairs(n)
+    with ap.Items.from_vectors(X1.cuda()) as it:
+        got = it.load_and_run(X2).cpu().numpy()
+        st = it.stats()
+        again = it.run_pairs().cpu().numpy()          # the set now holds X2
+        assert it.last_device_error() == 0
+    ref = oracle_lib.pearson(X2.numpy(), pi, pj)
+    assert np.all(np.abs(got - ref) <= pearson_tolerance(X2.numpy(), pi, pj, 1))
+    assert np.abs(got - again).max() <= 1e-7
+    assert st["reuse_R"] == 1.0 and st["h2d_bytes"] == n * D * 4
