@@ -297,14 +297,12 @@ overlap_kernel(Params P) {
                 const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
                 blF[p] = __fadd2_rn(blF[p], e);
                 if (MODE == GRAD) {
-                  // with d' = a' - b = -(dx, dy) and -e r = e * nr:
-                  // sum e r d' = sum (e nr) (dx, dy);
-                  // sum e r (x_b d'_y - y_b d'_x) = sum (e nr) (x_b dy - y_b dx)
+                  // per a-point sums of -e r, -e r x_b and -e r y_b (e nr = -e r);
+                  // the a'-dependent factors are applied once per a-point
                   const float2 ner = __fmul2_rn(e, nr);
-                  blX[p] = __ffma2_rn(ner, dx, blX[p]);
-                  blY[p] = __ffma2_rn(ner, dy, blY[p]);
-                  const float2 cr = __ffma2_rn(bx2, dy, __fmul2_rn(make_float2(-q.y, -q.y), dx));
-                  blT[p] = __ffma2_rn(ner, cr, blT[p]);
+                  blX[p] = __fadd2_rn(blX[p], ner);
+                  blY[p] = __ffma2_rn(ner, bx2, blY[p]);
+                  blT[p] = __ffma2_rn(ner, by2, blT[p]);
                 }
               }
             }
@@ -328,9 +326,17 @@ overlap_kernel(Params P) {
           for (int p = 0; p < R2; ++p) {
             vF = fmaf(aw2[p].x, accF[p].x, fmaf(aw2[p].y, accF[p].y, vF));
             if (MODE == GRAD) {
-              vX = fmaf(aw2[p].x, accX[p].x, fmaf(aw2[p].y, accX[p].y, vX));
-              vY = fmaf(aw2[p].x, accY[p].x, fmaf(aw2[p].y, accY[p].y, vY));
-              vT = fmaf(aw2[p].x, accT[p].x, fmaf(aw2[p].y, accT[p].y, vT));
+              // with S = sum -e r, Sx = sum -e r x_b, Sy = sum -e r y_b and
+              // -a' = (ntx, nty):  sum e r d'   = (Sx + ntx S, Sy + nty S),
+              // sum e r (x_b d'_y - y_b d'_x) = nty Sx - ntx Sy   (the b x b
+              // terms cancel)
+              const float2 gx = __ffma2_rn(ntx[p], accX[p], accY[p]);
+              const float2 gy = __ffma2_rn(nty[p], accX[p], accT[p]);
+              const float2 gt = __ffma2_rn(nty[p], accY[p],
+                                           __fmul2_rn(make_float2(-ntx[p].x, -ntx[p].y), accT[p]));
+              vX = fmaf(aw2[p].x, gx.x, fmaf(aw2[p].y, gx.y, vX));
+              vY = fmaf(aw2[p].x, gy.x, fmaf(aw2[p].y, gy.y, vY));
+              vT = fmaf(aw2[p].x, gt.x, fmaf(aw2[p].y, gt.y, vT));
             }
           }
 #pragma unroll

@@ -55,13 +55,21 @@ vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
     int cnt = 0;
     if (VEC4) {
       const float4 *x4 = reinterpret_cast<const float4 *>(x);
-      const int64_t n4 = D >> 2;
-      for (int64_t k = threadIdx.x; k < n4; k += blockDim.x) {
-        float4 v = __ldg(x4 + k);
-        part += (v.x + v.y) + (v.z + v.w);
-        if (++cnt == 16) { acc += (double)part; part = 0.f; cnt = 0; }
+      const int64_t n4 = D >> 2, st = blockDim.x;
+      int64_t k = threadIdx.x;
+      // four independent 16-byte loads in flight per thread
+      for (; k + 3 * st < n4; k += 4 * st) {
+        const float4 v0 = __ldg(x4 + k), v1 = __ldg(x4 + k + st);
+        const float4 v2 = __ldg(x4 + k + 2 * st), v3 = __ldg(x4 + k + 3 * st);
+        part += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w)) +
+                (((v2.x + v2.y) + (v2.z + v2.w)) + ((v3.x + v3.y) + (v3.z + v3.w)));
+        if (++cnt == 4) { acc += (double)part; part = 0.f; cnt = 0; }
       }
-      for (int64_t k = (n4 << 2) + threadIdx.x; k < D; k += blockDim.x) part += x[k];
+      for (; k < n4; k += st) {
+        const float4 v = __ldg(x4 + k);
+        part += (v.x + v.y) + (v.z + v.w);
+      }
+      for (int64_t e = (n4 << 2) + threadIdx.x; e < D; e += blockDim.x) part += x[e];
     } else {
       for (int64_t k = threadIdx.x; k < D; k += blockDim.x) {
         part += __ldg(x + k);
@@ -96,17 +104,28 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
     const float ml = (float)(m - (double)mh);
     double acc = 0.0;
     float psum = 0.f;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q4;
-         q += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t k = q << 2;
-      float v[4];
-      if (VEC4 && k + 3 < D) {
-        float4 t = __ldg(reinterpret_cast<const float4 *>(x + k));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-      } else {
+    const int64_t stq = (int64_t)gridDim.x * blockDim.x;
+    int iter = 0;
+    // two float4 groups per trip, both loads issued before either is used
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < q4; q0 += 2 * stq) {
+      float vv[2][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = (k + e < D) ? __ldg(x + k + e) : 0.f;
+      for (int u = 0; u < 2; ++u) {
+        const int64_t k = (q0 + u * stq) << 2;
+        if (VEC4 && k + 3 < D) {
+          const float4 t = __ldg(reinterpret_cast<const float4 *>(x + k));
+          vv[u][0] = t.x; vv[u][1] = t.y; vv[u][2] = t.z; vv[u][3] = t.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) vv[u][e] = (k + e < D) ? __ldg(x + k + e) : 0.f;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+      const int64_t q = q0 + u * stq;
+      if (q >= q4) break;
+      const int64_t k = q << 2;
+      const float *v = vv[u];
       float c[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) c[e] = (k + e < D) ? (v[e] - mh) - ml : 0.f;
@@ -131,8 +150,9 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
         const size_t o = blocked_offset(orow, k, nkb_32, kF32KBlock);
         *reinterpret_cast<float4 *>(c32 + o) = make_float4(c[0], c[1], c[2], c[3]);
       }
+      }
       // fold every 16 float4 (64 elements) into FP64
-      if (((q / ((int64_t)gridDim.x * blockDim.x)) & 15) == 15) { acc += (double)psum; psum = 0.f; }
+      if ((++iter & 7) == 0) { acc += (double)psum; psum = 0.f; }
     }
     acc += (double)psum;
     const double s = block_sum_f64(acc, red);
