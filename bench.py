@@ -242,7 +242,8 @@ def ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (32 GiB raw + 32 GiB hi/lo) far larger than L2"},
             "roofline": roofline, "gram_ms": gram_avg,
-            "gpu_launches": 3 * args.steps}
+            # per step: vec_mean, vec_split, vec_finalize, gram_tc
+            "gpu_launches": 4 * args.steps}
     if clk:
         line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
 
@@ -357,7 +358,6 @@ def run_ooc_workload(args):
         del Xd
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    # the host link as measured here (4 GiB pinned -> device)
     # the host link as measured here: macro-sized (3 GiB) pinned -> device
     # copies from eight places of the host set, best of them
     macro = 256 * D
@@ -376,6 +376,8 @@ def run_ooc_workload(args):
     link_gbs = max(rates)
     del probe
     items = ap.Items.from_vectors(Xh, slot_cache_bytes=OOC_CACHE)
+    if args.ooc_policy:
+        items.set_out_of_core_policy(args.ooc_policy)
     out = torch.empty(P, dtype=torch.float64, device="cuda")
     for _ in range(max(1, args.warmup)):
         items.run_pairs(out=out)
@@ -396,7 +398,8 @@ def run_ooc_workload(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
             "config": {"workload": "pearson_ooc_n8192_d3145728", "n_items": n, "dim": D,
-                       "host_bytes": n * D * 4, "slot_cache_bytes": OOC_CACHE},
+                       "host_bytes": n * D * 4, "slot_cache_bytes": OOC_CACHE,
+                       "policy": ["resident+streamed", "recursive+lru"][args.ooc_policy]},
             "reuse_R": st["reuse_R"], "slot_hit_rate": st["slot_hit_rate"],
             "h2d_bytes_per_step": st["h2d_bytes"], "h2d_gbs": h2d_gbs,
             "roofline": {"bound": "link", "achieved": h2d_gbs, "peak": link_gbs,
@@ -534,6 +537,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=512,
                     help="vectors in the oracle's bounded sample (all their pairs)")
+    ap.add_argument("--ooc-policy", type=int, default=0, choices=[0, 1],
+                    help="out-of-core schedule: 0 resident+streamed, 1 recursive order + LRU")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -242,18 +242,35 @@ ap_status ap_get_plan(const ap_items *items, ap_plan *out);
  * most), AP_ERR_UNSUPPORTED (vector sets). */
 ap_status ap_set_plan(ap_items *items, const ap_plan *plan);
 
+/* Out-of-core schedules. */
+typedef enum {
+  /* the default: a resident set of macros plus groups streamed past it,
+   * evicting the macro needed farthest ahead (the future is known) */
+  AP_OOC_RESIDENT_STREAM = 0,
+  /* the paper's policy: macro pairs in recursive quadrant order (Sec. IV-B),
+   * a miss loads into the least recently used slot (Sec. IV-A-1) */
+  AP_OOC_DC_LRU = 1
+} ap_ooc_policy;
+
+/* ap_set_out_of_core_policy -- rebuild an out-of-core handle's schedule with
+ * another policy (synchronises the device).  Errors: AP_ERR_INVALID_ARG
+ * (not a vector set, unknown policy), AP_ERR_STATE (not out of core). */
+ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy);
+
 /*
  * ap_plan_out_of_core -- host-only preview of the out-of-core schedule for n
  * vectors of length dim and a slot cache of slot_cache_bytes (the device cache
  * of Sec. IV-A, here holding pre-processed 256-item macros of 256*Dp*4 bytes,
- * Dp = dim rounded up to 64).  Builds the schedule, checks that every macro
- * pair is computed exactly once with both macros resident, and reports the
- * slots, the macro loads (R = loads / ceil(n/256), Sec. VI-A) and the steps.
- * Errors: AP_ERR_INVALID_ARG (bad sizes, NULL outputs, fewer than 3 slots
- * while the set does not fit), AP_ERR_STATE (schedule check failed).
+ * Dp = dim rounded up to 64) under `policy`.  Builds the schedule, checks that
+ * every macro pair is computed exactly once with both macros resident, and
+ * reports the slots, the macro loads (R = loads / ceil(n/256), Sec. VI-A) and
+ * the steps.  Errors: AP_ERR_INVALID_ARG (bad sizes or policy, NULL outputs,
+ * fewer than 3 slots while the set does not fit), AP_ERR_STATE (schedule check
+ * failed).
  */
 ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
-                              int64_t *n_slots, int64_t *n_loads, int64_t *n_steps);
+                              int32_t policy, int64_t *n_slots, int64_t *n_loads,
+                              int64_t *n_steps);
 
 /* Failure-path switches for testing the bounded device waits. */
 typedef enum {

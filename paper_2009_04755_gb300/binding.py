@@ -83,8 +83,9 @@ def lib():
             "ap_set_debug": (i32, [vp, i32, ctypes.c_uint64]),
             "ap_load_and_run": (i32, [vp, vp, vp, vp]),
             "ap_set_plan": (i32, [vp, ctypes.POINTER(Plan)]),
-            "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, ctypes.POINTER(i64),
+            "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, i32, ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "ap_set_out_of_core_policy": (i32, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -129,11 +130,15 @@ def plan_tiles(n: int, block: int):
     return out[:2 * cnt.value].reshape(-1, 2)
 
 
-def plan_out_of_core(n: int, dim: int, slot_cache_bytes: int) -> dict:
+AP_OOC_RESIDENT_STREAM, AP_OOC_DC_LRU = 0, 1
+
+
+def plan_out_of_core(n: int, dim: int, slot_cache_bytes: int, policy: int = 0) -> dict:
     """Host-only preview of the out-of-core schedule (slots, loads, steps)."""
     s, l, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    check(lib().ap_plan_out_of_core(int(n), int(dim), int(slot_cache_bytes), ctypes.byref(s),
-                                    ctypes.byref(l), ctypes.byref(t)), "ap_plan_out_of_core")
+    check(lib().ap_plan_out_of_core(int(n), int(dim), int(slot_cache_bytes), int(policy),
+                                    ctypes.byref(s), ctypes.byref(l), ctypes.byref(t)),
+          "ap_plan_out_of_core")
     return {"slots": s.value, "loads": l.value, "steps": t.value,
             "macros": (int(n) + 255) // 256}
 
@@ -283,6 +288,11 @@ class Items:
         st = RunStats()
         check(lib().ap_get_stats(self._h, ctypes.byref(st)), "ap_get_stats")
         return {k: getattr(st, k) for k, _ in RunStats._fields_}
+
+    def set_out_of_core_policy(self, policy: int):
+        """0: resident set + streamed groups (default); 1: the paper's
+        recursive order with LRU eviction."""
+        check(lib().ap_set_out_of_core_policy(self._h, int(policy)), "ap_set_out_of_core_policy")
 
     def set_debug(self, flags: int, wait_budget_ns: int = 0):
         """Failure-path switch (testing) and device wait budget (0 = 2 s)."""

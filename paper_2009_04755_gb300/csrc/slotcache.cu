@@ -172,6 +172,70 @@ static void build_units(VecStore &v, std::vector<int32_t> &units, std::vector<in
   }
 }
 
+// The paper's policy, for comparison: macro pairs in recursive quadrant
+// order (Sec. IV-B), each job loading what it misses into the least recently
+// used slot not needed by the job itself (Sec. IV-A-1).  A step ends at every
+// miss, so batches are as long as the run of hits.
+static void build_schedule_lru(VecStore &v) {
+  const int64_t M = v.n_macros, S = v.n_slots;
+  std::vector<int64_t> slot_of(M, -1), macro_in(S, -1), last_use(S, -1);
+  std::vector<int32_t> order;
+  dc_block_pairs(M, order);
+  v.steps.clear();
+  OocStep cur;
+  int64_t clock = 0;
+  for (size_t t = 0; t < order.size(); t += 2) {
+    const int64_t a = order[t], b = order[t + 1];
+    const bool miss = slot_of[a] < 0 || slot_of[b] < 0;
+    if (miss && !cur.pairs.empty()) {
+      v.steps.push_back(cur);
+      cur = OocStep();
+    }
+    for (int64_t m : {a, b}) {
+      if (slot_of[m] >= 0) continue;
+      int64_t victim = -1;
+      for (int64_t s = 0; s < S; ++s) {
+        const int64_t o = macro_in[s];
+        if (o < 0) { victim = s; break; }
+        if (o == a || o == b) continue;
+        if (victim < 0 || last_use[s] < last_use[victim]) victim = s;
+      }
+      if (macro_in[victim] >= 0) slot_of[macro_in[victim]] = -1;
+      macro_in[victim] = m;
+      slot_of[m] = victim;
+      cur.loads.push_back({(int32_t)m, (int32_t)victim});
+    }
+    ++clock;
+    last_use[slot_of[a]] = clock;
+    last_use[slot_of[b]] = clock;
+    cur.pairs.push_back({(int32_t)a, (int32_t)b, (int32_t)slot_of[a], (int32_t)slot_of[b]});
+  }
+  if (!cur.pairs.empty() || !cur.loads.empty()) v.steps.push_back(cur);
+}
+
+// Upload the units of v.steps (replacing earlier ones) and count loads/uses.
+static ap_status install_schedule(VecStore &v) {
+  std::vector<int32_t> units, cover;
+  build_units(v, units, cover);
+  dfree(v.d_units);
+  dfree(v.d_cover_units);
+  AP_TRY(dmalloc(&v.d_units, std::max<size_t>(units.size(), kOocTileInts)));
+  AP_TRY(dmalloc(&v.d_cover_units, std::max<size_t>(cover.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(v.d_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  if (!cover.empty())
+    AP_TRY(cudaMemcpy(v.d_cover_units, cover.data(), cover.size() * 4, cudaMemcpyHostToDevice));
+  v.ooc_loads = 0;
+  v.ooc_uses = 0;
+  for (const OocStep &st : v.steps) {
+    v.ooc_loads += (int64_t)st.loads.size();
+    std::set<int32_t> used;
+    for (const OocPair &pp : st.pairs) { used.insert(pp.a); used.insert(pp.b); }
+    v.ooc_uses += (int64_t)used.size();
+  }
+  return AP_OK;
+}
+
 ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
   VecStore &v = it->vec;
   if (!d->data_on_host) return AP_ERR_INVALID_ARG;
@@ -201,25 +265,9 @@ ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
     v.ev_raw_free.push_back(f);
   }
   v.ring_used.assign(v.ring, 0);
-  build_schedule(v);
-  std::vector<int32_t> units, cover;
-  build_units(v, units, cover);
-  AP_TRY(dmalloc(&v.d_units, std::max<size_t>(units.size(), kOocTileInts)));
-  AP_TRY(dmalloc(&v.d_cover_units, std::max<size_t>(cover.size(), kOocTileInts)));
-  if (!units.empty())
-    AP_TRY(cudaMemcpy(v.d_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
-  if (!cover.empty())
-    AP_TRY(cudaMemcpy(v.d_cover_units, cover.data(), cover.size() * 4, cudaMemcpyHostToDevice));
   AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(num_sms())));
-  v.ooc_loads = 0;
-  v.ooc_uses = 0;
-  for (const OocStep &st : v.steps) {
-    v.ooc_loads += (int64_t)st.loads.size();
-    std::set<int32_t> used;
-    for (const OocPair &pp : st.pairs) { used.insert(pp.a); used.insert(pp.b); }
-    v.ooc_uses += (int64_t)used.size();
-  }
-  return AP_OK;
+  build_schedule(v);
+  return install_schedule(v);
 }
 
 ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s) {
@@ -282,9 +330,23 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
 
 using namespace ap;
 
+extern "C" ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy) {
+  if (!items || items->kind != AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
+  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU) return AP_ERR_INVALID_ARG;
+  VecStore &v = items->vec;
+  if (!v.out_of_core) return AP_ERR_STATE;
+  const cudaError_t e = cudaDeviceSynchronize();     // the old units may be in use
+  if (e != cudaSuccess) return from_cuda(e);
+  if (policy == AP_OOC_DC_LRU) build_schedule_lru(v);
+  else build_schedule(v);
+  return install_schedule(v);
+}
+
 extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
-                                         int64_t *n_slots, int64_t *n_loads, int64_t *n_steps) {
+                                         int32_t policy, int64_t *n_slots, int64_t *n_loads,
+                                         int64_t *n_steps) {
   if (n_items < 0 || dim < 2 || !n_slots || !n_loads || !n_steps) return AP_ERR_INVALID_ARG;
+  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU) return AP_ERR_INVALID_ARG;
   VecStore v;
   v.n = n_items;
   v.D = dim;
@@ -294,7 +356,8 @@ extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t 
   v.n_slots = (int64_t)std::min<uint64_t>(slot_cache_bytes / slot_bytes, (uint64_t)v.n_macros);
   if (v.n_slots < 3 && v.n_slots < v.n_macros) return AP_ERR_INVALID_ARG;
   v.group = std::max<int64_t>(1, std::min<int64_t>(4, v.n_slots / 4));
-  build_schedule(v);
+  if (policy == AP_OOC_DC_LRU) build_schedule_lru(v);
+  else build_schedule(v);
   // every macro pair (a <= b) exactly once, both macros resident in the slots named
   std::vector<int32_t> seen((size_t)v.n_macros * v.n_macros, 0);
   std::vector<int64_t> holder(v.n_slots, -1);

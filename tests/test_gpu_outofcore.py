@@ -119,3 +119,23 @@ def test_load_and_run_matches_separate_calls(ap, oracle_lib, n, D):
     assert np.all(np.abs(got - ref) <= pearson_tolerance(X2.numpy(), pi, pj, 1))
     assert np.abs(got - again).max() <= 1e-7
     assert st["reuse_R"] == 1.0 and st["h2d_bytes"] == n * D * 4
+
+
+def test_out_of_core_lru_policy(ap, oracle_lib):
+    """The paper's policy (recursive order, LRU eviction) gives the same
+    correlations with more loads."""
+    n, D = 1300, 1024
+    X = synth.vectors_grouped(n, D, seed=31).pin_memory()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    with ap.Items.from_vectors(X, slot_cache_bytes=3 * _slot_bytes(D)) as it:
+        r0 = it.run_pairs().cpu().numpy()
+        R0 = it.stats()["reuse_R"]
+        it.set_out_of_core_policy(ap.binding.AP_OOC_DC_LRU)
+        r1 = it.run_pairs().cpu().numpy()
+        R1 = it.stats()["reuse_R"]
+        cnt = it.run_pairs(ap.AP_FN_COVERAGE).cpu().numpy()
+    tol = pearson_tolerance(X.numpy(), pi, pj, 1)
+    assert np.all(np.abs(r0 - ref) <= tol) and np.all(np.abs(r1 - ref) <= tol)
+    assert np.all(cnt == 1)
+    assert R1 >= R0 >= 1.0
