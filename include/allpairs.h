@@ -126,6 +126,16 @@ typedef struct ap_plan {
   int32_t reg_r;
   int32_t sorted;
   double rate;
+  /* vector sets only: 0 runs each 128 x 256 tile over all columns in one
+   * unit; k >= 1 splits every tile's columns into k ranges and runs them
+   * range by range inside waves of one tile per SM, so the tiles in flight
+   * read the same columns and share them in L2; the partial Grams meet in
+   * FP64 in the output, which a last pass scales by rs_i rs_j.  The default
+   * (set at creation, and by ap_set_plan with k_split = -1): ranges of about
+   * 16384 columns and at least two units per SM, at most one range per 64
+   * columns; 0 where that gives one range */
+  int32_t k_split;
+  int32_t reserved;
 } ap_plan;
 
 /*
@@ -235,11 +245,16 @@ ap_status ap_tune(ap_items *items, int32_t mode, void *stream, ap_plan *out);
 /* Current plan of a handle (vector sets report their fixed 128 x 256 tile). */
 ap_status ap_get_plan(const ap_items *items, ap_plan *out);
 
-/* Install a plan, e.g. a cached tuning result; `sorted` and `rate` are
- * ignored.  Synchronises the device.  Errors: AP_ERR_INVALID_ARG
- * (block_items outside 1..32, block_pts outside 64..8192, reg_r not 2 or 4
- * or too small for the largest item: 32 * reg_r * 128 points per item at
- * most), AP_ERR_UNSUPPORTED (vector sets). */
+/* Install a plan, e.g. a cached tuning result; `sorted`, `rate` and
+ * `reserved` are ignored.  Synchronises the device.
+ * Clouds: errors AP_ERR_INVALID_ARG (block_items outside 1..32, block_pts
+ * outside 64..8192, reg_r not 2 or 4 or too small for the largest item:
+ * 32 * reg_r * 128 points per item at most); k_split is ignored.
+ * Vector sets: block_items must be 128 and block_pts 256 (the fixed tile),
+ * reg_r is ignored and k_split (-1 for the default, or 0..AP_MAX_K_SPLIT)
+ * chooses the schedule of the split-BF16 Gram; errors AP_ERR_INVALID_ARG, AP_ERR_STATE (out-of-core
+ * or without the split-BF16 copy), AP_ERR_OOM. */
+#define AP_MAX_K_SPLIT 256
 ap_status ap_set_plan(ap_items *items, const ap_plan *plan);
 
 /* Out-of-core schedules. */

@@ -45,7 +45,8 @@ class RunStats(ctypes.Structure):
 
 class Plan(ctypes.Structure):
     _fields_ = [("block_items", ctypes.c_int32), ("block_pts", ctypes.c_int32),
-                ("reg_r", ctypes.c_int32), ("sorted", ctypes.c_int32), ("rate", ctypes.c_double)]
+                ("reg_r", ctypes.c_int32), ("sorted", ctypes.c_int32), ("rate", ctypes.c_double),
+                ("k_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class APError(RuntimeError):
@@ -280,8 +281,10 @@ class Items:
         check(lib().ap_get_plan(self._h, ctypes.byref(p)), "ap_get_plan")
         return {k: getattr(p, k) for k, _ in Plan._fields_}
 
-    def set_plan(self, block_items: int, block_pts: int, reg_r: int):
-        p = Plan(int(block_items), int(block_pts), int(reg_r), 0, 0.0)
+    def set_plan(self, block_items: int, block_pts: int, reg_r: int = 0, k_split: int = 0):
+        """Clouds: tile plan (block_items, block_pts, reg_r).  Vector sets:
+        (128, 256) and k_split, the schedule of the split-BF16 Gram."""
+        p = Plan(int(block_items), int(block_pts), int(reg_r), 0, 0.0, int(k_split), 0)
         check(lib().ap_set_plan(self._h, ctypes.byref(p)), "ap_set_plan")
 
     def stats(self) -> dict:

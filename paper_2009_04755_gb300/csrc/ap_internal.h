@@ -110,6 +110,10 @@ struct VecStore {
   std::vector<std::pair<int64_t, int64_t>> stream_cols;   // (first unit, units)
   // tile plans
   int32_t *d_tiles_tc = nullptr;  int64_t n_tiles_tc = 0;
+  // k_split > 0: the tiles run as split-K units in waves (panel_units)
+  int32_t k_split = 0;
+  int32_t *d_panel_units = nullptr; int64_t n_panel_units = 0;
+  std::vector<int32_t> h_tiles_tc;
   int32_t *d_tiles_f32 = nullptr; int64_t n_tiles_f32 = 0;
   void *tmap_hi = nullptr, *tmap_lo = nullptr;   // CUtensorMap (host copies)
   double *d_g64 = nullptr;          // FP64 partial sums of the tensor-core Gram
@@ -211,12 +215,25 @@ cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, 
 // begin, chunk end, unused}; chunks are 64 columns of D
 constexpr int kOocTileInts = 8;
 constexpr int kOocChunkCols = 64;
+constexpr int kMaxKSplit = AP_MAX_K_SPLIT;
+constexpr int64_t kKSplitCols = 16384;   // target columns per split-K unit
 // CTAs of one Gram launch and the FP64 scratch (doubles) it needs: one
 // 128 x 256 FP64 partial-sum tile per CTA
 int64_t tc_grid(int64_t n_tiles);
 size_t tc_scratch_doubles(int64_t n_tiles);
 void free_tc_tensor_maps(void *tmap_hi, void *tmap_lo);
 void tc_tiles(int64_t n, std::vector<int32_t> &tiles);   // (I-block of 128, J-block of 256)
+// split-K units of the tiles: waves of `group` tiles, column range-major
+// inside each wave (k_split ranges of the nchunks 64-column chunks)
+void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t group,
+                 int64_t k_split, std::vector<int32_t> &units);
+// the split-K schedule of a vector set's split-BF16 Gram: k_split column
+// ranges per tile (0 whole tiles, -1 the default rule of default_k_split)
+int32_t default_k_split(int64_t n_tiles, int64_t Dp);
+ap_status set_vector_plan(ap_items *it, int32_t k_split);
+// out[p] *= rs_i rs_j over the packed upper triangle (split-K partial sums
+// are added into out first)
+cudaError_t launch_gram_finalize(double *out, const double *rs, int64_t n, cudaStream_t s);
 
 // clouds (overlap.cu)
 cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,

@@ -49,6 +49,7 @@ void free_items(ap_items *it) {
   VecStore &v = it->vec;
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
+  dfree(v.d_panel_units);
   free_out_of_core(v);
   free_tc_tensor_maps(v.tmap_hi, v.tmap_lo);
   v.tmap_hi = v.tmap_lo = nullptr;
@@ -280,10 +281,13 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
     std::vector<int32_t> tiles;
     tc_tiles(v.n, tiles);
     v.n_tiles_tc = (int64_t)tiles.size() / 2;
+    v.h_tiles_tc = tiles;
     AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(v.n_tiles_tc)));
     AP_TRY(dmalloc(&v.d_tiles_tc, std::max<size_t>(tiles.size(), 2)));
     if (!tiles.empty())
       AP_TRY(cudaMemcpy(v.d_tiles_tc, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
+    ap_status st = set_vector_plan(it, -1);
+    if (st != AP_OK) return st;
   }
   if (v.precisions & (1u << AP_PREC_FP32)) {
     AP_TRY(dmalloc(&v.d_c32, elems));
@@ -417,7 +421,17 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
     if (cover) use_split = have_split;
     if (use_split && !have_split) return AP_ERR_STATE;
     if (!use_split && !have_f32) return AP_ERR_STATE;
-    if (use_split) {
+    if (use_split && !cover && v.k_split > 0) {
+      // split-K units in waves: partial Grams meet in FP64 in `out`
+      AP_TRY(cudaMemsetAsync(out, 0, (size_t)(n * (n - 1) / 2) * sizeof(double), s));
+      AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_panel_units,
+                            v.n_panel_units, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
+                            it->wait_budget_ns, it->debug, s));
+      AP_TRY(launch_gram_finalize(reinterpret_cast<double *>(out), v.d_rs, v.n, s));
+      it->stats.tiles = v.n_panel_units;
+      it->stats.tile_m = kTcTileM;
+      it->stats.tile_n = kTcTileN;
+    } else if (use_split) {
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_tiles_tc, v.n_tiles_tc,
                             it->d_queue, it->d_status, v.d_g64, out, cover, 0,
                             it->wait_budget_ns, it->debug, s));

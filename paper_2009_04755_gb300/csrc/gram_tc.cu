@@ -10,13 +10,16 @@
 // queue.  Warp roles inside the CTA:
 //   warp 0      one thread issues TMA tile loads (hi/lo of both blocks, 32
 //               columns per stage, 64-byte swizzle) into a 4-stage ring;
-//   warp 1      allocates 256 TMEM columns; one thread issues the three
-//               tcgen05.mma products per 16 columns into the TMEM accumulator
-//               and commits each stage back to the producer;
-//   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator, FP64
-//               scaling, packed upper-triangle stores.
-// Every wait is bounded (a per-launch budget, 2 s by default); when one runs out the CTA records a
-// device error code, drains its in-flight copies, frees TMEM and returns.
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators);
+//               one thread issues the three tcgen05.mma products per 16
+//               columns into one accumulator per 256-column chain and commits
+//               each stage back to the producer;
+//   warps 2-9   epilogue: tcgen05.ld of each finished chain into FP32
+//               register sums (FP64 every 16384 columns), then FP64 scaling
+//               and packed upper-triangle stores once per tile.
+// Every wait is bounded (a per-launch budget, 2 s by default); when one runs
+// out the CTA records a device error code, drains its in-flight copies, frees
+// TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,8 +41,12 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;   // 48 KB
 constexpr int TMEM_COLS = 2 * BN;            // two 128 x 256 FP32 accumulators
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter
 constexpr int NUM_THREADS = 32 * (2 + kEpiWarps);
-constexpr int kChunkStages = 2;              // one accumulation chain = 64 columns of D
-constexpr int kFlushChunks = 256;            // FP32 register sums -> FP64 every 16384 columns
+constexpr int kChainStages = 8;              // one accumulation chain = 256 columns of D
+constexpr int kHeadStages = 2;               // the first two chains of a unit: 64 columns
+constexpr float kSeedBeta = 0.9f;            // seed damping (see the epilogue)
+constexpr int kFlushCols = 16384;            // FP32 register sums -> FP64 every ~16384 columns
+constexpr int kFlushKb = kFlushCols / BK;
+constexpr int kUnitChunkStages = kOocChunkCols / BK;   // k-blocks per chunk of a split-K unit
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 
 // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
@@ -137,30 +144,55 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+
+
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-      "[%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-        "=r"(v[31])
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+// Chains of a unit's nkb k-blocks: two head chains of kHeadStages, then
+// chains of kChainStages; the last one may be shorter.
+__device__ __forceinline__ int64_t chain_first(int64_t c) {
+  return c < 2 ? c * kHeadStages : 2 * kHeadStages + (c - 2) * kChainStages;
+}
+__device__ __forceinline__ int64_t chain_stages(int64_t c, int64_t nkb) {
+  const int64_t len = c < 2 ? kHeadStages : kChainStages, left = nkb - chain_first(c);
+  return left < len ? left : len;
+}
+__device__ __forceinline__ int64_t chain_count(int64_t nkb) {
+  return nkb <= 2 * kHeadStages ? (nkb + kHeadStages - 1) / kHeadStages
+                                : 2 + (nkb - 2 * kHeadStages + kChainStages - 1) / kChainStages;
+}
 
-// Accumulate one 64-column chunk of D (two stages) per TMEM accumulator
+// Accumulate one 256-column chain of D (eight stages) per TMEM accumulator
 // (two accumulators, double-buffered), so the tensor core never carries a
-// long FP32 chain; eight epilogue warps drain each chunk into FP32 register
-// sums and fold those into FP64 scratch every kFlushChunks chunks.
+// long FP32 chain; eight epilogue warps drain each chain into FP32 register
+// sums and fold those into FP64 scratch every kFlushCols columns.  Chain
+// length trades the drain's cost against the accumulator's rounding: at
+// 8192 x 2^20, chains of 64 / 128 / 256 / 512 / 1024 columns took 183 / 165
+// / 156 / - / - ms (whole tiles) and 191 / 153 / 144 / 142 / 140 ms (64
+// column ranges per tile), while the bias on strongly correlated items
+// grows in proportion to the length (seeded chains, below, offset it).
 //
 // OOC = 1 (out-of-core units): each entry of `tiles` is kOocTileInts int32
 // {row block of A, row blocks of B (two), I block, J block, first chunk, end
-// chunk} -- row blocks index the slot pool the tensor maps cover, I/J the
+// chunk} (chunks of kOocChunkCols columns) -- row blocks index the slot pool the tensor maps cover, I/J the
 // item grid -- and the epilogue adds the unit's partial Gram into FP64
 // `out` (atomically: several K ranges of one tile may run at once).
 template <int COVER, int OOC>
@@ -213,11 +245,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
 
   // pipeline state (each role keeps its own copy)
   uint32_t p_stage = 0, p_phase = 0, m_stage = 0, m_phase = 0;
-  uint32_t cc = 0;                          // chunks consumed so far (accumulator ring)
-  uint32_t issued_parity[STAGES];
-  bool issued[STAGES];
-#pragma unroll
-  for (int s = 0; s < STAGES; ++s) { issued[s] = false; issued_parity[s] = 0; }
+  uint32_t cc = 0;                          // chains consumed so far (accumulator ring)
+  uint32_t issued_mask = 0, parity_mask = 0;   // stages with copies issued, and their phase
   const int64_t nk = Dp / BK;
   double *my_g64 = g64 + (size_t)blockIdx.x * (BN * BM);
 
@@ -231,14 +260,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
     const int64_t t = *s_tile;
     if (t >= n_tiles) break;
     int32_t i0, j0, rb_a, rb_b, rb_b1;
-    int64_t c_begin = 0, nchunks = COVER ? 0 : nk / kChunkStages;
+    // this tile's (or unit's) k-blocks [kb0, kb0 + nkb) and its chains of
+    // kChainStages k-blocks (the last one may be shorter)
+    int64_t kb0 = 0, nkb = COVER ? 0 : nk;
     if (OOC) {
       const int32_t *u = tiles + (size_t)kOocTileInts * t;
       rb_a = u[0]; rb_b = u[1]; rb_b1 = u[2];
       i0 = u[3] * BM;
       j0 = u[4] * BN;
-      c_begin = u[5];
-      nchunks = COVER ? 0 : (int64_t)(u[6] - u[5]);
+      kb0 = (int64_t)u[5] * kUnitChunkStages;
+      nkb = COVER ? 0 : (int64_t)(u[6] - u[5]) * kUnitChunkStages;
     } else {
       i0 = tiles[2 * t] * BM;
       j0 = tiles[2 * t + 1] * BN;
@@ -247,10 +278,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       rb_b1 = rb_b + 1;
     }
 
+    const int64_t nchains = chain_count(nkb);
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer ----------------
-      const int64_t kb0 = c_begin * kChunkStages;
-      for (int64_t kb = kb0; kb < kb0 + nchunks * kChunkStages; ++kb) {
+      for (int64_t kb = kb0; kb < kb0 + nkb; ++kb) {
         if (!mbar_wait(empty_bar(p_stage), p_phase ^ 1, s_abort, budget)) {
           atomicCAS(status, 0, DEV_TIMEOUT_EMPTY);
           *s_abort = 1;
@@ -272,14 +303,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         tma_load_block(sb + 2 * A_BYTES + A_BYTES, &tm_hi, fb, k, rb_b1);
         tma_load_block(sb + 2 * A_BYTES + B_BYTES, &tm_lo, fb, k, rb_b);
         tma_load_block(sb + 2 * A_BYTES + B_BYTES + A_BYTES, &tm_lo, fb, k, rb_b1);
-        issued[p_stage] = true;
-        issued_parity[p_stage] = p_phase;
+        issued_mask |= 1u << p_stage;
+        parity_mask = (parity_mask & ~(1u << p_stage)) | (p_phase << p_stage);
         if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- MMA issuer ----------------
       uint32_t mc = cc;
-      for (int64_t c = 0; c < nchunks && !*s_abort; ++c, ++mc) {
+      for (int64_t c = 0; c < nchains && !*s_abort; ++c, ++mc) {
         const uint32_t a = mc & 1, use = mc >> 1;
         if (!mbar_wait(tempty_bar(a), (use & 1) ^ 1, s_abort, budget)) {
           atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
@@ -289,7 +320,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         tc_fence_after();
         const uint32_t dt = tmem + a * BN;
         bool ok = true;
-        for (int s = 0; s < kChunkStages; ++s) {
+        // chains 0 and 1 start from zero; later ones from the seed the
+        // epilogue left in this accumulator
+        const int64_t stages = chain_stages(c, nkb);
+        const uint32_t seeded = c >= 2 ? 1u : 0u;
+        for (int s = 0; s < stages; ++s) {
           if (!mbar_wait(full_bar(m_stage), m_phase, s_abort, budget)) {
             atomicCAS(status, 0, DEV_TIMEOUT_FULL);
             *s_abort = 1;
@@ -305,7 +340,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
             const uint32_t off = kk * 32;    // 16 bf16 = 32 bytes inside the swizzle atom
             const uint64_t dah = sw64_desc(a_hi + off), dal = sw64_desc(a_lo + off);
             const uint64_t dbh = sw64_desc(b_hi + off), dbl = sw64_desc(b_lo + off);
-            umma_bf16(dt, dah, dbh, (s | kk) != 0 ? 1u : 0u);
+            umma_bf16(dt, dah, dbh, (seeded | s | kk) != 0 ? 1u : 0u);
             umma_bf16(dt, dah, dbl, 1u);
             umma_bf16(dt, dal, dbh, 1u);
           }
@@ -313,7 +348,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
           if (++m_stage == STAGES) { m_stage = 0; m_phase ^= 1; }
         }
         if (!ok) break;
-        umma_commit(tfull_bar(a));          // fires when this chunk's MMAs have landed
+        umma_commit(tfull_bar(a));          // fires when this chain's MMAs have landed
       }
     } else if (warp >= 2) {
       // ---------------- epilogue ----------------
@@ -326,7 +361,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       for (int c = 0; c < BN / 2; ++c) sum[c] = 0.f;
       bool flushed = false, ok = true;
       uint32_t ec = cc;
-      for (int64_t c = 0; c < nchunks; ++c, ++ec) {
+      int64_t kb_since = 0;                  // k-blocks summed since the last flush
+      for (int64_t c = 0; c < nchains; ++c, ++ec) {
         const uint32_t a = ec & 1, use = ec >> 1;
         if (!mbar_wait(tfull_bar(a), use & 1, s_abort, budget)) {
           if (lane == 0) atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
@@ -336,18 +372,44 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + a * BN + h * (BN / 2);
+        const int64_t len = chain_stages(c, nkb);
+        kb_since += len;
+        // The tensor core aligns the addends of each accumulate step to the
+        // largest exponent, truncating what falls below a few guard bits,
+        // and rounds the sum toward zero; a chain whose sum grows one way
+        // (correlated items) therefore comes out short by an amount growing
+        // with its length and with |accumulator|.  Chain c + 2 in this
+        // accumulator starts from -g, g = kSeedBeta x R_c (this chain's
+        // drained value, scaled to the next chain's length), and the register
+        // sum takes +g: the seeds settle near g = 0.47 S (S a chain's sum), so
+        // the accumulator runs from about -S/2 to +S/2, the round-toward-zero
+        // errors of its two halves cancel and the alignment losses, which
+        // scale with |accumulator|, halve.  Correlated pairs (r ~ 0.99) at
+        // 16384 columns per unit, measured with unseeded chains and modelled
+        // with the adder above: chains of 64 columns -2.4e-7, 256 columns
+        // -8.7e-7, 256 seeded -1.3e-7.
+        const bool seed = c + 2 < nchains;
+        const float ratio =
+            seed ? kSeedBeta * (float)chain_stages(c + 2, nkb) / (float)len : 0.f;
 #pragma unroll
-        for (int m = 0; m < BN / 2 / 32; ++m) {
-          uint32_t v[32];
-          tmem_ld32(taddr + m * 32, v);
+        for (int m = 0; m < BN / 2 / 16; ++m) {
+          uint32_t v[16];
+          tmem_ld16(taddr + m * 16, v);
 #pragma unroll
-          for (int e = 0; e < 32; ++e) sum[m * 32 + e] += __uint_as_float(v[e]);
+          for (int e = 0; e < 16; ++e) {     // ratio 0 (no seed): g = 0, sum += r
+            const float r = __uint_as_float(v[e]), g = r * ratio;
+            sum[m * 16 + e] += r + g;
+            v[e] = __float_as_uint(-g);
+          }
+          if (seed) tmem_st16(taddr + m * 16, v);
         }
+        if (seed) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty_bar(a)) : "memory");
-        if ((c + 1) % kFlushChunks == 0 && c + 1 < nchunks) {
+        if (kb_since >= kFlushKb && c + 1 < nchains) {
+          kb_since = 0;
           // fold the FP32 partial sums into FP64 scratch ([col][row] layout)
 #pragma unroll
           for (int e = 0; e < BN / 2; ++e) {
@@ -381,16 +443,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         }
       }
     }
-    cc += (uint32_t)nchunks;
+    cc += (uint32_t)nchains;
     __syncthreads();
   }
 
   // teardown: the producer drains copies still in flight after an abort
   if (warp == 0 && lane == 0 && *s_abort) {
     for (int s = 0; s < STAGES; ++s) {
-      if (!issued[s]) continue;
+      if (!((issued_mask >> s) & 1u)) continue;
       const uint64_t t0 = global_ns();
-      while (!mbar_try_wait(full_bar(s), issued_parity[s])) {
+      while (!mbar_try_wait(full_bar(s), (parity_mask >> s) & 1u)) {
         if (global_ns() - t0 > budget) break;
       }
     }

@@ -86,4 +86,27 @@ void tc_tiles(int64_t n, std::vector<int32_t> &tiles) {
   }
 }
 
+void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t group,
+                 int64_t k_split, std::vector<int32_t> &units) {
+  // waves of `group` consecutive tiles; inside a wave, column range p of
+  // every tile before range p + 1 of any, so the tiles running at one time
+  // stream the same columns of their rows
+  units.clear();
+  const int64_t nt = (int64_t)tiles.size() / 2;
+  k_split = std::max<int64_t>(1, std::min<int64_t>(k_split, nchunks));
+  for (int64_t w0 = 0; w0 < nt; w0 += group) {
+    const int64_t w1 = std::min<int64_t>(nt, w0 + group);
+    for (int64_t p = 0; p < k_split; ++p) {
+      const int32_t c0 = (int32_t)(p * nchunks / k_split);
+      const int32_t c1 = (int32_t)((p + 1) * nchunks / k_split);
+      for (int64_t t = w0; t < w1; ++t) {
+        const int32_t ib = tiles[2 * t], jb = tiles[2 * t + 1];
+        const int32_t rb = jb * (kTcTileN / kTcTileM);
+        const int32_t u[kOocTileInts] = {ib, rb, rb + 1, ib, jb, c0, c1, 0};
+        units.insert(units.end(), u, u + kOocTileInts);
+      }
+    }
+  }
+}
+
 }  // namespace ap

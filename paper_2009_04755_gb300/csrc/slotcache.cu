@@ -49,6 +49,13 @@ __global__ void ooc_finalize_kernel(double *__restrict__ out, const double *__re
 
 }  // namespace
 
+cudaError_t launch_gram_finalize(double *out, const double *rs, int64_t n, cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>(n - 1, 65535);
+  ooc_finalize_kernel<<<grid, 256, 0, s>>>(out, rs, n);
+  return cudaGetLastError();
+}
+
 void free_out_of_core(VecStore &v) {
   dfree(v.d_pool_hi);
   dfree(v.d_pool_lo);

@@ -74,12 +74,15 @@ using namespace ap;
 
 extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
   if (!it || !out) return AP_ERR_INVALID_ARG;
+  out->k_split = 0;
+  out->reserved = 0;
   if (it->kind == AP_ITEMS_VECTOR) {
     out->block_items = kTcTileM;
     out->block_pts = kTcTileN;
     out->reg_r = 0;
     out->sorted = 0;
     out->rate = 0.0;
+    out->k_split = it->vec.k_split;
     return AP_OK;
   }
   out->block_items = it->cl.block_items;
@@ -90,9 +93,50 @@ extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
   return AP_OK;
 }
 
+int32_t ap::default_k_split(int64_t n_tiles, int64_t Dp) {
+  // column ranges of about kKSplitCols columns, and at least two units per SM
+  const int64_t nch = Dp / kOocChunkCols;
+  int64_t k = (Dp + kKSplitCols - 1) / kKSplitCols;
+  if (n_tiles > 0) k = std::max<int64_t>(k, (2LL * num_sms() + n_tiles - 1) / n_tiles);
+  k = std::min<int64_t>(k, std::min<int64_t>(nch, kMaxKSplit));
+  return k <= 1 ? 0 : (int32_t)k;
+}
+
+// vector sets: (re)build the split-K wave units of the tensor-core tiles
+ap_status ap::set_vector_plan(ap_items *it, int32_t k_split) {
+  VecStore &v = it->vec;
+  if (v.out_of_core) return AP_ERR_STATE;
+  if (!v.d_hi) return AP_ERR_STATE;
+  if (k_split < 0) k_split = default_k_split(v.n_tiles_tc, v.Dp);
+  cudaError_t e = cudaDeviceSynchronize();      // the old units may still be in use
+  if (e != cudaSuccess) return from_cuda(e);
+  dfree(v.d_panel_units);
+  v.n_panel_units = 0;
+  v.k_split = 0;
+  if (k_split == 0) return AP_OK;
+  std::vector<int32_t> units;
+  panel_units(v.h_tiles_tc, v.Dp / kOocChunkCols, tc_grid(v.n_tiles_tc), k_split, units);
+  const int64_t nu = (int64_t)units.size() / kOocTileInts;
+  if (tc_grid(nu) > tc_grid(v.n_tiles_tc)) {
+    // more CTAs than the whole-tile launch: one FP64 scratch tile each
+    dfree(v.d_g64);
+    AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(nu)));
+  }
+  AP_TRY(dmalloc(&v.d_panel_units, std::max<size_t>(units.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(v.d_panel_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  v.n_panel_units = nu;
+  v.k_split = k_split;
+  return AP_OK;
+}
+
 extern "C" ap_status ap_set_plan(ap_items *it, const ap_plan *plan) {
   if (!it || !plan) return AP_ERR_INVALID_ARG;
-  if (it->kind == AP_ITEMS_VECTOR) return AP_ERR_UNSUPPORTED;
+  if (it->kind == AP_ITEMS_VECTOR) {
+    if (plan->block_items != kTcTileM || plan->block_pts != kTcTileN) return AP_ERR_INVALID_ARG;
+    if (plan->k_split < -1 || plan->k_split > kMaxKSplit) return AP_ERR_INVALID_ARG;
+    return set_vector_plan(it, plan->k_split);
+  }
   if (plan->block_items < 1 || plan->block_items > kOverlapMaxBlockItems) return AP_ERR_INVALID_ARG;
   if (plan->block_pts < 64 || plan->block_pts > 8192) return AP_ERR_INVALID_ARG;
   if (plan->reg_r != 2 && plan->reg_r != 4) return AP_ERR_INVALID_ARG;

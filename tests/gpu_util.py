@@ -33,6 +33,35 @@ def pearson_tolerance(X, pi, pj, prec):
         return PEARSON_ATOL + 6 * 2.0 ** -16 * num / np.sqrt(ss[pi] * ss[pj])
     r = np.einsum("pk,pk->p", C[pi], C[pj]) / np.sqrt(ss[pi] * ss[pj])
     return PEARSON_ATOL + 2.0 ** -22 * np.sqrt(D) * np.abs(r)
+def regroup_tolerance(X, pi, pj, chain=256):
+    """Allowance between two split-BF16 results that differ only in how the
+    same products are grouped into tensor-core chains (whole tiles against
+    split-K units, resident against out-of-core).
+
+    A chain adds at most 3 * chain products in FP32; each partial sum rounds
+    with relative error <= 2^-23 (2^-24 round-to-nearest, 2^-23 if the
+    accumulator truncates), a random walk of about 2^-23 sqrt(3 chain) S_c
+    for a chain whose |products| sum to S_c.  Chains round independently, so
+    one result is off by about 2^-23 sqrt(3 chain) sqrt(sum_c S_c^2); two
+    results, and a factor 4 for the tail: 8 * 2^-23 sqrt(3 chain)
+    sqrt(sum_c S_c^2) / sqrt(ss_i ss_j).  A lost or doubled 64-column range
+    moves r by about its share of sum |c_i c_j|, orders of magnitude more.
+    """
+    X = np.asarray(X, np.float64)
+    C = np.abs(X - X.mean(1, keepdims=True))
+    n, D = C.shape
+    ss = (C * C).sum(1)
+    nc = (D + chain - 1) // chain
+    Cp = np.zeros((n, nc * chain))
+    Cp[:, :D] = C
+    out = np.empty(len(pi))
+    m = max(1, (1 << 24) // (nc * chain))
+    for a in range(0, len(pi), m):
+        b = min(len(pi), a + m)
+        S = (Cp[pi[a:b]] * Cp[pj[a:b]]).reshape(b - a, nc, chain).sum(-1)
+        out[a:b] = np.sqrt((S * S).sum(1))
+    return 1e-12 + 8 * 2.0 ** -23 * np.sqrt(3 * chain) * out / np.sqrt(ss[pi] * ss[pj])
+
 # adjoint: norm-wise, |g - g_ref|_inf <= 1e-4 max(|g_ref|_inf, 1e-6 sum w w)
 GRAD_RTOL = 1e-4
 

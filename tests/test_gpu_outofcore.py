@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import PEARSON_ATOL, pearson_tolerance
+from gpu_util import PEARSON_ATOL, pearson_tolerance, regroup_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -53,9 +53,10 @@ def test_out_of_core_matches_in_hbm_path(ap):
         r_hbm = it.run_pairs().cpu().numpy()
     with ap.Items.from_vectors(X.pin_memory(), slot_cache_bytes=3 * _slot_bytes(D) + 1) as it:
         r_ooc = it.run_pairs().cpu().numpy()
-    # same products; only the grouping of the FP32 chunk sums differs (K is
-    # split into ranges whose sums meet in FP64): ~2^-24 sqrt(chunks) relative
-    assert np.abs(r_hbm - r_ooc).max() <= 1e-7
+    # same products; only their grouping into FP32 chains differs (K is split
+    # into ranges whose sums meet in FP64)
+    pi, pj = np.triu_indices(n, 1)
+    assert np.all(np.abs(r_hbm - r_ooc) <= regroup_tolerance(X.numpy(), pi, pj))
 
 
 def test_out_of_core_coverage(ap):
@@ -117,7 +118,7 @@ def test_load_and_run_matches_separate_calls(ap, oracle_lib, n, D):
         assert it.last_device_error() == 0
     ref = oracle_lib.pearson(X2.numpy(), pi, pj)
     assert np.all(np.abs(got - ref) <= pearson_tolerance(X2.numpy(), pi, pj, 1))
-    assert np.abs(got - again).max() <= 1e-7
+    assert np.all(np.abs(got - again) <= regroup_tolerance(X2.numpy(), pi, pj))
     assert st["reuse_R"] == 1.0 and st["h2d_bytes"] == n * D * 4
 
 

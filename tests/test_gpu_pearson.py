@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import PEARSON_ATOL, pearson_tolerance
+from gpu_util import PEARSON_ATOL, pearson_tolerance, regroup_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -168,3 +168,36 @@ def test_pearson_full_size_sampled(ap, oracle_lib):
         assert torch.isfinite(r_tc).all() and torch.isfinite(r_32).all()
         # every correlation is a correlation
         assert float(r_tc.abs().max()) <= 1.0
+
+
+@pytest.mark.parametrize("n,D,ks", [(1000, 3000, [1, 3, 16]), (130, 200, [64]),
+                                    (300, 20000, [1, 2])])
+def test_pearson_k_split_schedule(ap, oracle_lib, n, D, ks):
+    """Split-K units in waves give the whole-tile result: the same products,
+    only the grouping of the FP32 chain sums into FP64 differs."""
+    X = synth.vectors_grouped(n, D, seed=5 * n + D)
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    tol = pearson_tolerance(X.numpy(), pi, pj, 1)
+    tol_regroup = regroup_tolerance(X.numpy(), pi, pj)
+    with ap.Items.from_vectors(X.cuda()) as it:
+        default = it.plan()["k_split"]
+        assert default >= 0
+        it.set_plan(128, 256, 0, 0)
+        base = it.run_pairs().cpu().numpy()
+        assert np.all(np.abs(base - ref) <= tol)
+        for k in ks + [-1]:
+            it.set_plan(128, 256, 0, k)
+            assert it.plan()["k_split"] == (default if k < 0 else k)
+            got = it.run_pairs().cpu().numpy()
+            assert it.last_device_error() == 0
+            assert np.all(np.abs(got - ref) <= tol), float(np.abs(got - ref).max())
+            assert np.all(np.abs(got - base) <= tol_regroup)
+            cnt = it.run_pairs(ap.AP_FN_COVERAGE).cpu().numpy()
+            assert np.all(cnt == 1)
+        it.set_plan(128, 256, 0, 0)
+        again = it.run_pairs().cpu().numpy()
+        np.testing.assert_array_equal(again, base)
+        for bad in [(128, 256, 0, -2), (128, 256, 0, 10 ** 6), (64, 256, 0, 4)]:
+            with pytest.raises(ap.APError):
+                it.set_plan(*bad)
