@@ -30,9 +30,10 @@ N_ITEMS, DIM = 8192, 1 << 20
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram launch at
-# 8192 x 2^20, captured at full size (a one-pass metric set) on the kernel
-# as it stands; None whenever the kernel has changed since the capture
-GRAM_TRAFFIC_BYTES = 723495411968 + 18084992000
+# 8192 x 2^20 with its default schedule (64 column ranges per tile), captured
+# at full size (a one-pass metric set) on the kernel as it stands; None
+# whenever the kernel has changed since the capture
+GRAM_TRAFFIC_BYTES = 305428372992 + 17525829632
 
 
 def peaks():
@@ -230,7 +231,8 @@ def ours(args):
     peak_tf = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
     flops_launch = 3 * 2.0 * D * P          # three BF16 products per pair, 2 flops per MAC
     achieved_tf = flops_launch / (gram_avg / 1e3) / 1e12
-    traffic = None if GRAM_TRAFFIC_BYTES is None else GRAM_TRAFFIC_BYTES
+    # the capture covers the default 8192 x 2^20 schedule only
+    traffic = GRAM_TRAFFIC_BYTES if (n, D, k_split) == (N_ITEMS, DIM, 64) else None
     roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
                 "kernel": "gram_tc_kernel", "peak_kind": f"{pk_kind} bf16 sustained",

@@ -98,7 +98,7 @@ struct VecStore {
   int64_t n_macros = 0, n_slots = 0, group = 0, ring = 0;
   __nv_bfloat16 *d_pool_hi = nullptr, *d_pool_lo = nullptr;   // slot pool, blocked layout
   float *d_raw = nullptr;                                      // raw staging ring
-  std::vector<cudaEvent_t> ev_raw_ready, ev_raw_free;
+  std::vector<cudaEvent_t> ev_raw_ready, ev_raw_free, ev_prepped;
   std::vector<int> ring_used;
   std::vector<OocStep> steps;
   int32_t *d_units = nullptr, *d_cover_units = nullptr;
@@ -152,6 +152,7 @@ struct ap_items {
   ap_run_stats stats{};
   int32_t last_dev_error = 0;
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t prep_stream = nullptr;    // pre-processing of streamed macros (load-and-run)
   cudaStream_t graph_stream = nullptr;   // private stream the graphs are captured on
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint64_t plan_version = 0;

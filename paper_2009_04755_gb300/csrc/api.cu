@@ -58,6 +58,7 @@ void free_items(ap_items *it) {
   clear_graphs(it);
   if (it->graph_stream) cudaStreamDestroy(it->graph_stream);
   if (it->copy_stream) cudaStreamDestroy(it->copy_stream);
+  if (it->prep_stream) cudaStreamDestroy(it->prep_stream);
   for (cudaEvent_t *e : {&it->ev_a, &it->ev_b})
     if (*e) cudaEventDestroy(*e);
   delete it;
@@ -282,7 +283,9 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
     tc_tiles(v.n, tiles);
     v.n_tiles_tc = (int64_t)tiles.size() / 2;
     v.h_tiles_tc = tiles;
-    AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(v.n_tiles_tc)));
+    // one FP64 scratch tile per SM: every Gram launch (whole tiles, split-K
+    // units, streamed columns) has at most one CTA per SM
+    AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(num_sms())));
     AP_TRY(dmalloc(&v.d_tiles_tc, std::max<size_t>(tiles.size(), 2)));
     if (!tiles.empty())
       AP_TRY(cudaMemcpy(v.d_tiles_tc, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));

@@ -66,8 +66,10 @@ void free_out_of_core(VecStore &v) {
   v.stream_cols.clear();
   for (cudaEvent_t e : v.ev_raw_ready) cudaEventDestroy(e);
   for (cudaEvent_t e : v.ev_raw_free) cudaEventDestroy(e);
+  for (cudaEvent_t e : v.ev_prepped) cudaEventDestroy(e);
   v.ev_raw_ready.clear();
   v.ev_raw_free.clear();
+  v.ev_prepped.clear();
   free_tc_tensor_maps(v.tmap_pool_hi, v.tmap_pool_lo);
   v.tmap_pool_hi = v.tmap_pool_lo = nullptr;
 }
@@ -403,16 +405,15 @@ static ap_status build_stream_units(VecStore &v) {
         if (i0 >= v.n || i0 >= jmax) continue;
         tiles.push_back({(int32_t)ib, (int32_t)(2 * m), (int32_t)m});
       }
+    // the column's tiles as split-K units in waves, like the resident
+    // schedule (column ranges of ~16384 columns, two units per SM at least)
     const int64_t T = (int64_t)tiles.size();
-    int64_t ks = T > 0 ? (2LL * num_sms() + T - 1) / T : 1;
-    ks = std::max<int64_t>(1, std::min<int64_t>(ks, std::min<int64_t>(32, nch)));
+    std::vector<int32_t> pairs, col_units;
+    for (const auto &t : tiles) { pairs.push_back(t[0]); pairs.push_back(t[2]); }
+    const int64_t ks = std::max<int32_t>(1, default_k_split(T, v.Dp));
+    panel_units(pairs, nch, num_sms(), ks, col_units);
     const int64_t u0 = (int64_t)units.size() / kOocTileInts;
-    for (const auto &t : tiles)
-      for (int64_t k = 0; k < ks; ++k) {
-        const int32_t c0 = (int32_t)(k * nch / ks), c1 = (int32_t)((k + 1) * nch / ks);
-        const int32_t u[kOocTileInts] = {t[0], t[1], t[1] + 1, t[0], t[2], c0, c1, 0};
-        units.insert(units.end(), u, u + kOocTileInts);
-      }
+    units.insert(units.end(), col_units.begin(), col_units.end());
     v.stream_cols.push_back({u0, (int64_t)units.size() / kOocTileInts - u0});
   }
   AP_TRY(dmalloc(&v.d_stream_units, std::max<size_t>(units.size(), kOocTileInts)));
@@ -428,22 +429,34 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
     if (st != AP_OK) return st;
   }
   if (!v.d_raw) {
-    v.ring = 2;
+    // raw staging ring: up to 8 GiB of macros, so the copies run ahead of
+    // the Gram instead of waiting for each column's compute
+    const int64_t macro_bytes = kMacro * v.ld * 4;
+    v.ring = std::max<int64_t>(2, std::min<int64_t>({(8LL << 30) / macro_bytes, 16,
+                                                     (int64_t)v.stream_cols.size()}));
     AP_TRY(dmalloc(&v.d_raw, (size_t)v.ring * kMacro * v.ld));
     for (int64_t b = 0; b < v.ring; ++b) {
-      cudaEvent_t a, f;
+      cudaEvent_t a, f, p;
       AP_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
       v.ev_raw_ready.push_back(a);
       AP_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
       v.ev_raw_free.push_back(f);
+      AP_TRY(cudaEventCreateWithFlags(&p, cudaEventDisableTiming));
+      v.ev_prepped.push_back(p);
     }
     v.ring_used.assign(v.ring, 0);
   }
+  if (!it->prep_stream)
+    AP_TRY(cudaStreamCreateWithFlags(&it->prep_stream, cudaStreamNonBlocking));
   const int64_t P = v.n * (v.n - 1) / 2;
   AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
+  // earlier work on s may still read the rows about to be overwritten
   AP_TRY(cudaEventRecord(it->ev_a, s));
   AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
+  AP_TRY(cudaStreamWaitEvent(it->prep_stream, it->ev_a, 0));
   const bool split = v.d_hi != nullptr, f32 = v.d_c32 != nullptr;
+  // three streams: copies (copy_stream) -> pre-processing (prep_stream) ->
+  // Gram column m (s), linked by per-slot events
   for (size_t m = 0; m < v.stream_cols.size(); ++m) {
     const int64_t b = (int64_t)(m % v.ring);
     const int64_t r0 = (int64_t)m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
@@ -452,13 +465,15 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
     AP_TRY(cudaMemcpyAsync(raw, h + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
                            cudaMemcpyHostToDevice, it->copy_stream));
     AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
-    AP_TRY(cudaStreamWaitEvent(s, v.ev_raw_ready[b], 0));
-    AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, s));
+    AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[b], 0));
+    AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, it->prep_stream));
     AP_TRY(launch_vec_split(raw, r0, r0, rows, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
                             split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
-                            v.d_rs, s));
-    AP_TRY(cudaEventRecord(v.ev_raw_free[b], s));
+                            v.d_rs, it->prep_stream));
+    AP_TRY(cudaEventRecord(v.ev_raw_free[b], it->prep_stream));
+    AP_TRY(cudaEventRecord(v.ev_prepped[b], it->prep_stream));
     v.ring_used[b] = 1;
+    AP_TRY(cudaStreamWaitEvent(s, v.ev_prepped[b], 0));
     AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs,
                           v.d_stream_units + v.stream_cols[m].first * kOocTileInts,
                           v.stream_cols[m].second, it->d_queue, it->d_status, v.d_g64, out, 0, 1,

@@ -117,11 +117,6 @@ ap_status ap::set_vector_plan(ap_items *it, int32_t k_split) {
   std::vector<int32_t> units;
   panel_units(v.h_tiles_tc, v.Dp / kOocChunkCols, tc_grid(v.n_tiles_tc), k_split, units);
   const int64_t nu = (int64_t)units.size() / kOocTileInts;
-  if (tc_grid(nu) > tc_grid(v.n_tiles_tc)) {
-    // more CTAs than the whole-tile launch: one FP64 scratch tile each
-    dfree(v.d_g64);
-    AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(nu)));
-  }
   AP_TRY(dmalloc(&v.d_panel_units, std::max<size_t>(units.size(), kOocTileInts)));
   if (!units.empty())
     AP_TRY(cudaMemcpy(v.d_panel_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));

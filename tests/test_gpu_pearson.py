@@ -201,3 +201,26 @@ def test_pearson_k_split_schedule(ap, oracle_lib, n, D, ks):
         for bad in [(128, 256, 0, -2), (128, 256, 0, 10 ** 6), (64, 256, 0, 4)]:
             with pytest.raises(ap.APError):
                 it.set_plan(*bad)
+
+
+@pytest.mark.parametrize("k_split", [0, -1])
+def test_pearson_correlated_bias(ap, oracle_lib, k_split):
+    """Strongly correlated and anti-correlated pairs over long vectors: the
+    tensor core's truncating accumulation biases each chain toward zero in
+    proportion to its length (~9e-7 for unseeded 256-column chains at
+    r ~ 0.99); seeded chains must keep the mean error of either sign within
+    3e-7 and every pair within 1e-6."""
+    n, D = 32, 1 << 18
+    g = torch.Generator().manual_seed(11)
+    base = torch.randn(1, D, generator=g)
+    sign = torch.where(torch.rand(n, 1, generator=g) < 0.5, -1.0, 1.0)
+    X = (sign * base + 0.05 * torch.randn(n, D, generator=g)).float()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    with ap.Items.from_vectors(X.cuda()) as it:
+        it.set_plan(128, 256, 0, k_split)
+        got = it.run_pairs().cpu().numpy()
+    d = got - ref
+    assert np.abs(ref).min() > 0.99
+    assert abs(d[ref > 0].mean()) <= 3e-7 and abs(d[ref < 0].mean()) <= 3e-7
+    assert np.abs(d).max() <= PEARSON_ATOL
