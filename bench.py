@@ -404,7 +404,8 @@ def run_ooc_workload(args):
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
             "config": {"workload": "pearson_ooc_n8192_d3145728", "n_items": n, "dim": D,
                        "host_bytes": n * D * 4, "slot_cache_bytes": OOC_CACHE,
-                       "policy": ["resident+streamed", "recursive+lru"][args.ooc_policy]},
+                       "policy": ["resident+streamed", "recursive+lru",
+                                  "column-slices"][args.ooc_policy]},
             "reuse_R": st["reuse_R"], "slot_hit_rate": st["slot_hit_rate"],
             "h2d_bytes_per_step": st["h2d_bytes"], "h2d_gbs": h2d_gbs,
             "roofline": {"bound": "link", "achieved": h2d_gbs, "peak": link_gbs,
@@ -546,8 +547,9 @@ def main():
     ap.add_argument("--k-split", type=int, default=-1,
                     help="Pearson Gram schedule: column ranges per tile (0 whole tiles; "
                          "-1 the library default)")
-    ap.add_argument("--ooc-policy", type=int, default=0, choices=[0, 1],
-                    help="out-of-core schedule: 0 resident+streamed, 1 recursive order + LRU")
+    ap.add_argument("--ooc-policy", type=int, default=2, choices=[0, 1, 2],
+                    help="out-of-core schedule: 0 resident+streamed, 1 recursive order + LRU, "
+                         "2 column slices")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

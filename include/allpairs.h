@@ -264,12 +264,25 @@ typedef enum {
   AP_OOC_RESIDENT_STREAM = 0,
   /* the paper's policy: macro pairs in recursive quadrant order (Sec. IV-B),
    * a miss loads into the least recently used slot (Sec. IV-A-1) */
-  AP_OOC_DC_LRU = 1
+  AP_OOC_DC_LRU = 1,
+  /* column slices: the same chunk of columns of every item resident at once
+   * (one chunk buffer, plus a ring of raw pieces that lets the next chunk's
+   * copy overlap this chunk's Gram), the Gram accumulated over the chunks in
+   * FP64; each
+   * item crosses the host link once (R = 1).  The Gram is a sum over
+   * columns, so this schedule is open to the correlation only: rows are
+   * centred on a shift (the mean of their first chunk) and the exact mean,
+   * variance and centred Gram follow from the shifted sums at the end */
+  AP_OOC_K_SLICED = 2
 } ap_ooc_policy;
 
 /* ap_set_out_of_core_policy -- rebuild an out-of-core handle's schedule with
- * another policy (synchronises the device).  Errors: AP_ERR_INVALID_ARG
- * (not a vector set, unknown policy), AP_ERR_STATE (not out of core). */
+ * another policy (synchronises the device).  Switching between the macro
+ * schedules (0, 1) and the column slices (2) frees one kind of buffer and
+ * allocates the other within the same slot_cache_bytes.  Errors:
+ * AP_ERR_INVALID_ARG (not a vector set, unknown policy, cache too small for
+ * a column chunk of 64 columns), AP_ERR_STATE (not out of core),
+ * AP_ERR_OOM. */
 ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy);
 
 /*
@@ -279,9 +292,10 @@ ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy);
  * Dp = dim rounded up to 64) under `policy`.  Builds the schedule, checks that
  * every macro pair is computed exactly once with both macros resident, and
  * reports the slots, the macro loads (R = loads / ceil(n/256), Sec. VI-A) and
- * the steps.  Errors: AP_ERR_INVALID_ARG (bad sizes or policy, NULL outputs,
- * fewer than 3 slots while the set does not fit), AP_ERR_STATE (schedule check
- * failed).
+ * the steps.  AP_OOC_K_SLICED reports 1 slot (its chunk buffer), one load
+ * per macro and one step per column chunk.  Errors: AP_ERR_INVALID_ARG (bad
+ * sizes or policy, NULL outputs, fewer than 3 slots while the set does not
+ * fit), AP_ERR_STATE (schedule check failed).
  */
 ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
                               int32_t policy, int64_t *n_slots, int64_t *n_loads,

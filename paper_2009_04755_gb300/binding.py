@@ -131,7 +131,7 @@ def plan_tiles(n: int, block: int):
     return out[:2 * cnt.value].reshape(-1, 2)
 
 
-AP_OOC_RESIDENT_STREAM, AP_OOC_DC_LRU = 0, 1
+AP_OOC_RESIDENT_STREAM, AP_OOC_DC_LRU, AP_OOC_K_SLICED = 0, 1, 2
 
 
 def plan_out_of_core(n: int, dim: int, slot_cache_bytes: int, policy: int = 0) -> dict:
@@ -294,7 +294,7 @@ class Items:
 
     def set_out_of_core_policy(self, policy: int):
         """0: resident set + streamed groups (default); 1: the paper's
-        recursive order with LRU eviction."""
+        recursive order with LRU eviction; 2: column slices (R = 1)."""
         check(lib().ap_set_out_of_core_policy(self._h, int(policy)), "ap_set_out_of_core_policy")
 
     def set_debug(self, flags: int, wait_budget_ns: int = 0):

@@ -104,6 +104,16 @@ struct VecStore {
   int32_t *d_units = nullptr, *d_cover_units = nullptr;
   void *tmap_pool_hi = nullptr, *tmap_pool_lo = nullptr;
   int64_t ooc_loads = 0, ooc_uses = 0;
+  // out-of-core, column-sliced schedule (AP_OOC_K_SLICED): every item's
+  // chunk of slice_cols columns resident at once in one chunk buffer ([0])
+  int32_t ooc_policy = 0;
+  int64_t slice_cols = 0, n_slices = 0;
+  __nv_bfloat16 *d_slice_hi[2] = {nullptr, nullptr}, *d_slice_lo[2] = {nullptr, nullptr};
+  void *tmap_slice_hi[2] = {nullptr, nullptr}, *tmap_slice_lo[2] = {nullptr, nullptr};
+  double *d_shift = nullptr, *d_part_c = nullptr, *d_delta = nullptr;
+  int32_t *d_slice_units = nullptr; int64_t n_slice_units = 0;
+  int32_t *d_slice_cover = nullptr; int64_t n_slice_cover = 0;   // one unit per tile
+  cudaEvent_t ev_slice_ready[2] = {nullptr, nullptr}, ev_slice_done[2] = {nullptr, nullptr};
   // streamed load-and-run of a resident set: per macro column m, the split-K
   // units of the pairs (a <= m, m) on the resident blocked arrays
   int32_t *d_stream_units = nullptr;
@@ -198,6 +208,18 @@ cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, do
 cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D, int64_t ld,
                              int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                              float *c32, double *part, double *ss, double *rs, cudaStream_t s);
+// one column chunk [.., cols) of rows row0.., centred on per-row shifts (the
+// rows' blocked copies hold cols_p >= cols columns); FP64 partials of
+// sum c^2 and sum c are set (first_chunk) or accumulated per row
+cudaError_t launch_vec_split_slice(const float *X, int64_t row0, int64_t n, int64_t cols,
+                                   int64_t ld, int64_t cols_p, const double *shift,
+                                   __nv_bfloat16 *hi, __nv_bfloat16 *lo, double *part,
+                                   double *part_c, int first_chunk, cudaStream_t s);
+// after the last chunk: delta_i = mu_i - s_i, ss, rs, and
+// out[p] = (out[p] - D delta_i delta_j) rs_i rs_j
+cudaError_t launch_slice_finalize(const double *part, const double *part_c, int64_t n,
+                                  int64_t D, double *delta, double *ss, double *rs, double *out,
+                                  cudaStream_t s);
 cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
                             const int32_t *tiles, int64_t n_tiles, int32_t *queue,
                             void *out, int coverage, int64_t row0, int64_t n_total,
@@ -258,6 +280,13 @@ int num_sms();
 // shared host helpers (api.cu, tune.cu)
 // ---------------------------------------------------------------------------
 ap_status from_cuda(cudaError_t e);
+// propagate an ap_status
+#define AP_TRY_ST(expr)                            \
+  do {                                             \
+    ap_status _s = (expr);                         \
+    if (_s != AP_OK) return _s;                    \
+  } while (0)
+
 #define AP_TRY(expr)                               \
   do {                                             \
     cudaError_t _e = (expr);                       \

@@ -56,22 +56,66 @@ cudaError_t launch_gram_finalize(double *out, const double *rs, int64_t n, cudaS
   return cudaGetLastError();
 }
 
-void free_out_of_core(VecStore &v) {
-  dfree(v.d_pool_hi);
-  dfree(v.d_pool_lo);
+static void free_raw_ring(VecStore &v) {
   dfree(v.d_raw);
-  dfree(v.d_units);
-  dfree(v.d_cover_units);
-  dfree(v.d_stream_units);
-  v.stream_cols.clear();
   for (cudaEvent_t e : v.ev_raw_ready) cudaEventDestroy(e);
   for (cudaEvent_t e : v.ev_raw_free) cudaEventDestroy(e);
   for (cudaEvent_t e : v.ev_prepped) cudaEventDestroy(e);
   v.ev_raw_ready.clear();
   v.ev_raw_free.clear();
   v.ev_prepped.clear();
+  v.ring_used.clear();
+  v.ring = 0;
+}
+
+static ap_status alloc_raw_ring(VecStore &v, int64_t ring, size_t floats_each) {
+  v.ring = ring;
+  AP_TRY(dmalloc(&v.d_raw, (size_t)ring * floats_each));
+  for (int64_t b = 0; b < ring; ++b) {
+    cudaEvent_t a, f;
+    AP_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    v.ev_raw_ready.push_back(a);
+    AP_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
+    v.ev_raw_free.push_back(f);
+  }
+  v.ring_used.assign(ring, 0);
+  return AP_OK;
+}
+
+static void free_pool(VecStore &v) {
+  dfree(v.d_pool_hi);
+  dfree(v.d_pool_lo);
+  dfree(v.d_units);
+  dfree(v.d_cover_units);
   free_tc_tensor_maps(v.tmap_pool_hi, v.tmap_pool_lo);
   v.tmap_pool_hi = v.tmap_pool_lo = nullptr;
+  v.steps.clear();
+}
+
+static void free_slices(VecStore &v) {
+  for (int b = 0; b < 2; ++b) {
+    dfree(v.d_slice_hi[b]);
+    dfree(v.d_slice_lo[b]);
+    free_tc_tensor_maps(v.tmap_slice_hi[b], v.tmap_slice_lo[b]);
+    v.tmap_slice_hi[b] = v.tmap_slice_lo[b] = nullptr;
+    if (v.ev_slice_ready[b]) cudaEventDestroy(v.ev_slice_ready[b]);
+    if (v.ev_slice_done[b]) cudaEventDestroy(v.ev_slice_done[b]);
+    v.ev_slice_ready[b] = v.ev_slice_done[b] = nullptr;
+  }
+  dfree(v.d_shift);
+  dfree(v.d_part_c);
+  dfree(v.d_delta);
+  dfree(v.d_slice_units);
+  dfree(v.d_slice_cover);
+  v.n_slice_units = v.n_slice_cover = 0;
+}
+
+void free_out_of_core(VecStore &v) {
+  free_pool(v);
+  free_slices(v);
+  free_raw_ring(v);
+  dfree(v.d_stream_units);
+  v.stream_cols.clear();
 }
 
 // Build the load / compute schedule for M macros and S slots.
@@ -245,6 +289,155 @@ static ap_status install_schedule(VecStore &v) {
   return AP_OK;
 }
 
+// the slot pool of the macro schedules (AP_OOC_RESIDENT_STREAM, AP_OOC_DC_LRU)
+static ap_status alloc_pool(VecStore &v) {
+  const int64_t pool_rows = 2 * kRowBlock * v.n_slots;
+  AP_TRY(dmalloc(&v.d_pool_hi, (size_t)pool_rows * v.Dp));
+  AP_TRY(dmalloc(&v.d_pool_lo, (size_t)pool_rows * v.Dp));
+  AP_TRY(cudaMemset(v.d_pool_hi, 0, (size_t)pool_rows * v.Dp * 2));
+  AP_TRY(cudaMemset(v.d_pool_lo, 0, (size_t)pool_rows * v.Dp * 2));
+  AP_TRY_ST(alloc_raw_ring(v, std::max<int64_t>(2, v.group), (size_t)kMacro * v.ld));
+  AP_TRY(make_tc_tensor_maps(v.d_pool_hi, v.d_pool_lo, pool_rows, v.Dp, &v.tmap_pool_hi,
+                             &v.tmap_pool_lo));
+  return AP_OK;
+}
+
+// Column slices.  The Gram's CTAs leave no room on an SM for the
+// pre-processing kernels, which therefore run between Gram launches; what
+// overlaps the Gram of one chunk is the copy of the next.  So: one hi/lo
+// chunk buffer of all rows and a raw ring of kMacro-row pieces, a whole chunk
+// when the cache allows (at least 64K columns per chunk), else four pieces.
+// Chunk width is a multiple of 64; chunks of equal width cover Dp.
+static bool slice_geometry(int64_t n, int64_t Dp, uint64_t budget, int64_t *cols,
+                           int64_t *count, int64_t *ring) {
+  if (n < 1) return false;
+  const int64_t rows = (n + kRowBlock - 1) / kRowBlock * kRowBlock;
+  const int64_t pieces = (n + kMacro - 1) / kMacro;
+  for (int64_t r : {pieces, std::min<int64_t>(pieces, 4)}) {
+    const uint64_t per_col = 4ull * rows + 4ull * kMacro * r;
+    const int64_t cmax = (int64_t)(budget / per_col) / kOocChunkCols * kOocChunkCols;
+    const bool last = r == std::min<int64_t>(pieces, 4);
+    if (cmax >= std::min<int64_t>(Dp, 65536) || (last && cmax >= kOocChunkCols)) {
+      *count = (Dp + cmax - 1) / cmax;
+      *cols = ((Dp + *count - 1) / *count + kOocChunkCols - 1) / kOocChunkCols * kOocChunkCols;
+      *ring = r;
+      return true;
+    }
+  }
+  return false;
+}
+
+static ap_status alloc_slices(VecStore &v) {
+  int64_t ring = 0;
+  if (!slice_geometry(v.n, v.Dp, v.slot_cache_bytes, &v.slice_cols, &v.n_slices, &ring))
+    return AP_ERR_INVALID_ARG;
+  const int64_t rows = (v.n + kRowBlock - 1) / kRowBlock * kRowBlock;
+  const size_t elems = (size_t)rows * v.slice_cols;
+  AP_TRY(dmalloc(&v.d_slice_hi[0], elems));
+  AP_TRY(dmalloc(&v.d_slice_lo[0], elems));
+  AP_TRY(cudaMemset(v.d_slice_hi[0], 0, elems * 2));
+  AP_TRY(cudaMemset(v.d_slice_lo[0], 0, elems * 2));
+  AP_TRY(make_tc_tensor_maps(v.d_slice_hi[0], v.d_slice_lo[0], v.n, v.slice_cols,
+                             &v.tmap_slice_hi[0], &v.tmap_slice_lo[0]));
+  AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_ready[0], cudaEventDisableTiming));
+  AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_done[0], cudaEventDisableTiming));
+  AP_TRY(dmalloc(&v.d_shift, (size_t)v.n));
+  AP_TRY(dmalloc(&v.d_delta, (size_t)v.n));
+  AP_TRY(dmalloc(&v.d_part_c, (size_t)v.n * kSplitParts));
+  AP_TRY_ST(alloc_raw_ring(v, ring, (size_t)kMacro * v.slice_cols));
+  // every tile of the triangle, split-K units in waves over one chunk
+  std::vector<int32_t> tiles, units;
+  tc_tiles(v.n, tiles);
+  const int64_t nt = (int64_t)tiles.size() / 2;
+  const int64_t nch = v.slice_cols / kOocChunkCols;
+  panel_units(tiles, nch, num_sms(), std::max<int32_t>(1, default_k_split(nt, v.slice_cols)),
+              units);
+  v.n_slice_units = (int64_t)units.size() / kOocTileInts;
+  AP_TRY(dmalloc(&v.d_slice_units, std::max<size_t>(units.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(v.d_slice_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  std::vector<int32_t> cover;
+  panel_units(tiles, nch, num_sms(), 1, cover);
+  v.n_slice_cover = (int64_t)cover.size() / kOocTileInts;
+  AP_TRY(dmalloc(&v.d_slice_cover, std::max<size_t>(cover.size(), kOocTileInts)));
+  if (!cover.empty())
+    AP_TRY(cudaMemcpy(v.d_slice_cover, cover.data(), cover.size() * 4, cudaMemcpyHostToDevice));
+  return AP_OK;
+}
+
+// The column-sliced run: chunk c of every row is copied (strided, in pieces
+// of kMacro rows) on the copy stream, centred on a per-row shift (the mean of
+// the row's first chunk) and split on the prep stream into the chunk buffer
+// once the Gram of chunk c - 1 has finished with it, and the Gram of all
+// tiles over chunk c adds its FP64 partials on s; each item crosses the host
+// link once (R = 1).  The shifted-data identities turn the accumulated sums
+// into the centred Gram at the end.
+static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t s) {
+  VecStore &v = it->vec;
+  const int64_t P = v.n * (v.n - 1) / 2;
+  if (coverage) {
+    AP_TRY(launch_gram_tc(v.tmap_slice_hi[0], v.tmap_slice_lo[0], v.n, v.slice_cols, v.d_rs,
+                          v.d_slice_cover, v.n_slice_cover, it->d_queue, it->d_status, v.d_g64,
+                          out, 1, 1, it->wait_budget_ns, it->debug, s));
+    it->stats.tiles = v.n_slice_cover;
+    it->stats.item_loads = 0;
+    it->stats.reuse_R = 0.0;
+    it->stats.h2d_bytes = 0;
+    it->stats.slot_hit_rate = 1.0;
+    return AP_OK;
+  }
+  if (!it->prep_stream)
+    AP_TRY(cudaStreamCreateWithFlags(&it->prep_stream, cudaStreamNonBlocking));
+  AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
+  AP_TRY(cudaEventRecord(it->ev_a, s));
+  AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
+  AP_TRY(cudaStreamWaitEvent(it->prep_stream, it->ev_a, 0));
+  std::fill(v.ring_used.begin(), v.ring_used.end(), 0);
+  int64_t seq = 0;
+  const int b = 0;                          // the chunk buffer
+  for (int64_t c = 0; c < v.n_slices; ++c) {
+    const int64_t c0 = c * v.slice_cols;
+    const int64_t cols = std::max<int64_t>(0, std::min<int64_t>(v.slice_cols, v.D - c0));
+    if (c >= 1) AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_slice_done[b], 0));
+    for (int64_t r0 = 0; r0 < v.n; r0 += kMacro) {
+      const int64_t rows = std::min<int64_t>(kMacro, v.n - r0);
+      const int64_t rb = seq++ % v.ring;
+      float *raw = v.d_raw + (size_t)rb * kMacro * v.slice_cols;
+      if (v.ring_used[rb]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[rb], 0));
+      if (cols > 0)
+        AP_TRY(cudaMemcpy2DAsync(raw, (size_t)v.slice_cols * 4, v.h_src + (size_t)r0 * v.ld + c0,
+                                 (size_t)v.ld * 4, (size_t)cols * 4, (size_t)rows,
+                                 cudaMemcpyHostToDevice, it->copy_stream));
+      AP_TRY(cudaEventRecord(v.ev_raw_ready[rb], it->copy_stream));
+      AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[rb], 0));
+      if (c == 0)
+        AP_TRY(launch_vec_mean(raw, rows, std::max<int64_t>(cols, 1), v.slice_cols,
+                               v.d_shift + r0, it->prep_stream));
+      AP_TRY(launch_vec_split_slice(raw, r0, rows, cols, v.slice_cols, v.slice_cols, v.d_shift,
+                                    v.d_slice_hi[b], v.d_slice_lo[b], v.d_part, v.d_part_c,
+                                    c == 0 ? 1 : 0, it->prep_stream));
+      AP_TRY(cudaEventRecord(v.ev_raw_free[rb], it->prep_stream));
+      v.ring_used[rb] = 1;
+    }
+    AP_TRY(cudaEventRecord(v.ev_slice_ready[b], it->prep_stream));
+    AP_TRY(cudaStreamWaitEvent(s, v.ev_slice_ready[b], 0));
+    AP_TRY(launch_gram_tc(v.tmap_slice_hi[b], v.tmap_slice_lo[b], v.n, v.slice_cols, v.d_rs,
+                          v.d_slice_units, v.n_slice_units, it->d_queue, it->d_status, v.d_g64,
+                          out, 0, 1, it->wait_budget_ns, it->debug, s));
+    AP_TRY(cudaEventRecord(v.ev_slice_done[b], s));
+  }
+  AP_TRY(launch_slice_finalize(v.d_part, v.d_part_c, v.n, v.D, v.d_delta, v.d_ss, v.d_rs,
+                               reinterpret_cast<double *>(out), s));
+  it->stats.tiles = v.n_slice_units * v.n_slices;
+  it->stats.tile_m = kTcTileM;
+  it->stats.tile_n = kTcTileN;
+  it->stats.item_loads = v.n;
+  it->stats.reuse_R = 1.0;
+  it->stats.h2d_bytes = (uint64_t)v.n * v.D * 4;
+  it->stats.slot_hit_rate = 1.0;
+  return AP_OK;
+}
+
 ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
   VecStore &v = it->vec;
   if (!d->data_on_host) return AP_ERR_INVALID_ARG;
@@ -257,30 +450,16 @@ ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
   v.n_slots = (int64_t)std::min<uint64_t>(d->slot_cache_bytes / slot_bytes, (uint64_t)v.n_macros);
   if (v.n_slots < 3 && v.n_slots < v.n_macros) return AP_ERR_INVALID_ARG;   // cache too small
   v.group = std::max<int64_t>(1, std::min<int64_t>(4, v.n_slots / 4));
-  v.ring = std::max<int64_t>(2, v.group);
-  const int64_t pool_rows = 2 * kRowBlock * v.n_slots;
-  AP_TRY(dmalloc(&v.d_pool_hi, (size_t)pool_rows * v.Dp));
-  AP_TRY(dmalloc(&v.d_pool_lo, (size_t)pool_rows * v.Dp));
-  AP_TRY(cudaMemset(v.d_pool_hi, 0, (size_t)pool_rows * v.Dp * 2));
-  AP_TRY(cudaMemset(v.d_pool_lo, 0, (size_t)pool_rows * v.Dp * 2));
-  AP_TRY(dmalloc(&v.d_raw, (size_t)v.ring * kMacro * v.ld));
-  AP_TRY(make_tc_tensor_maps(v.d_pool_hi, v.d_pool_lo, pool_rows, v.Dp, &v.tmap_pool_hi,
-                             &v.tmap_pool_lo));
-  for (int64_t b = 0; b < v.ring; ++b) {
-    cudaEvent_t a, f;
-    AP_TRY(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
-    v.ev_raw_ready.push_back(a);
-    AP_TRY(cudaEventCreateWithFlags(&f, cudaEventDisableTiming));
-    v.ev_raw_free.push_back(f);
-  }
-  v.ring_used.assign(v.ring, 0);
   AP_TRY(dmalloc(&v.d_g64, tc_scratch_doubles(num_sms())));
+  v.ooc_policy = AP_OOC_RESIDENT_STREAM;
+  AP_TRY_ST(alloc_pool(v));
   build_schedule(v);
   return install_schedule(v);
 }
 
 ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s) {
   VecStore &v = it->vec;
+  if (v.ooc_policy == AP_OOC_K_SLICED) return run_slices(it, out, coverage, s);
   const int64_t P = v.n * (v.n - 1) / 2;
   if (!coverage) AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
   // copies must follow whatever the caller queued before this call
@@ -341,11 +520,29 @@ using namespace ap;
 
 extern "C" ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy) {
   if (!items || items->kind != AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
-  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU) return AP_ERR_INVALID_ARG;
+  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU && policy != AP_OOC_K_SLICED)
+    return AP_ERR_INVALID_ARG;
   VecStore &v = items->vec;
   if (!v.out_of_core) return AP_ERR_STATE;
-  const cudaError_t e = cudaDeviceSynchronize();     // the old units may be in use
+  const cudaError_t e = cudaDeviceSynchronize();     // the old buffers may be in use
   if (e != cudaSuccess) return from_cuda(e);
+  const bool was_sliced = v.ooc_policy == AP_OOC_K_SLICED;
+  const bool sliced = policy == AP_OOC_K_SLICED;
+  if (sliced) {
+    // validate before giving up the slot pool
+    int64_t cols, count, ring;
+    if (!slice_geometry(v.n, v.Dp, v.slot_cache_bytes, &cols, &count, &ring))
+      return AP_ERR_INVALID_ARG;
+  }
+  if (sliced != was_sliced) {
+    // the two kinds of schedule keep different buffers within the same budget
+    free_pool(v);
+    free_slices(v);
+    free_raw_ring(v);
+  }
+  v.ooc_policy = policy;
+  if (sliced) return was_sliced ? AP_OK : alloc_slices(v);
+  if (was_sliced) AP_TRY_ST(alloc_pool(v));
   if (policy == AP_OOC_DC_LRU) build_schedule_lru(v);
   else build_schedule(v);
   return install_schedule(v);
@@ -355,7 +552,18 @@ extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t 
                                          int32_t policy, int64_t *n_slots, int64_t *n_loads,
                                          int64_t *n_steps) {
   if (n_items < 0 || dim < 2 || !n_slots || !n_loads || !n_steps) return AP_ERR_INVALID_ARG;
-  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU) return AP_ERR_INVALID_ARG;
+  if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU && policy != AP_OOC_K_SLICED)
+    return AP_ERR_INVALID_ARG;
+  if (policy == AP_OOC_K_SLICED) {
+    // one chunk buffer; every macro loaded once; one step per column chunk
+    int64_t cols, count, ring;
+    if (!slice_geometry(n_items, (dim + 63) / 64 * 64, slot_cache_bytes, &cols, &count, &ring))
+      return AP_ERR_INVALID_ARG;
+    *n_slots = 1;
+    *n_loads = (n_items + kMacro - 1) / kMacro;
+    *n_steps = count;
+    return AP_OK;
+  }
   VecStore v;
   v.n = n_items;
   v.D = dim;

@@ -86,12 +86,16 @@ vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
 // mu_hi + mu_lo), write the blocked split-BF16 and/or FP32 copies (zero
 // padded to Dp columns) and this CTA's FP64 partial of sum_k c_k^2.
 // Grid: x = kSplitParts column ranges of a row, y = rows (strided).
-template <bool VEC4>
+// SLICE: one column chunk of the rows, centred on a per-row shift instead of
+// the mean; the CTA's partials of sum c^2 and sum c are added to `part` and
+// `part_c` (set when first_chunk) so they accumulate over the chunks.
+template <bool VEC4, bool SLICE>
 __global__ void __launch_bounds__(kSplitThreads)
 vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, int64_t n,
                  int64_t D, int64_t ld, int64_t Dp, const double *__restrict__ mu,
                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
-                 float *__restrict__ c32, double *__restrict__ part) {
+                 float *__restrict__ c32, double *__restrict__ part,
+                 double *__restrict__ part_c, int first_chunk) {
   __shared__ double red[33];
   const int64_t q4 = Dp >> 2;                  // float4 groups per padded row
   const int64_t nkb_tc = Dp / kTcKBlock, nkb_32 = Dp / kF32KBlock;
@@ -102,8 +106,8 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
     const double m = mu[row];
     const float mh = (float)m;
     const float ml = (float)(m - (double)mh);
-    double acc = 0.0;
-    float psum = 0.f;
+    double acc = 0.0, acc_c = 0.0;
+    float psum = 0.f, psum_c = 0.f;
     const int64_t stq = (int64_t)gridDim.x * blockDim.x;
     int iter = 0;
     // two float4 groups per trip, both loads issued before either is used
@@ -130,6 +134,7 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
 #pragma unroll
       for (int e = 0; e < 4; ++e) c[e] = (k + e < D) ? (v[e] - mh) - ml : 0.f;
       psum += (c[0] * c[0] + c[1] * c[1]) + (c[2] * c[2] + c[3] * c[3]);
+      if (SLICE) psum_c += (c[0] + c[1]) + (c[2] + c[3]);
       if (hi) {
         __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -152,11 +157,25 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
       }
       }
       // fold every 16 float4 (64 elements) into FP64
-      if ((++iter & 7) == 0) { acc += (double)psum; psum = 0.f; }
+      if ((++iter & 7) == 0) {
+        acc += (double)psum;
+        psum = 0.f;
+        if (SLICE) { acc_c += (double)psum_c; psum_c = 0.f; }
+      }
     }
     acc += (double)psum;
     const double s = block_sum_f64(acc, red);
-    if (threadIdx.x == 0) part[row * gridDim.x + blockIdx.x] = s;
+    const size_t slot = (size_t)row * gridDim.x + blockIdx.x;
+    if (SLICE) {
+      acc_c += (double)psum_c;
+      const double sc = block_sum_f64(acc_c, red);
+      if (threadIdx.x == 0) {
+        part[slot] = first_chunk ? s : part[slot] + s;
+        part_c[slot] = first_chunk ? sc : part_c[slot] + sc;
+      }
+    } else if (threadIdx.x == 0) {
+      part[slot] = s;
+    }
   }
 }
 
@@ -172,6 +191,39 @@ __global__ void vec_finalize_kernel(const double *__restrict__ part, int64_t row
     ss[row] = s;
     // zero variance: correlation undefined, propagate NaN
     rs[row] = s > 0.0 ? 1.0 / sqrt(s) : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// Column-sliced rows centred on shifts s_i: with S1 = sum_k c_ik and
+// S2 = sum_k c_ik^2 over all D columns (c = x - s), delta_i = mu_i - s_i =
+// S1 / D and ss_i = S2 - S1 delta_i (the shifted-data form of the variance).
+__global__ void slice_stats_kernel(const double *__restrict__ part,
+                                   const double *__restrict__ part_c, int64_t n, int nparts,
+                                   int64_t D, double *__restrict__ delta,
+                                   double *__restrict__ ss, double *__restrict__ rs) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+      s1 += part_c[row * nparts + b];
+      s2 += part[row * nparts + b];
+    }
+    const double d = s1 / (double)D, v = s2 - s1 * d;
+    delta[row] = d;
+    ss[row] = v;
+    rs[row] = v > 0.0 ? 1.0 / sqrt(v) : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// r_ij = (G_ij - D delta_i delta_j) rs_i rs_j over the packed upper triangle,
+// G the Gram of the shifted rows (the centred Gram is G - D delta_i delta_j)
+__global__ void slice_finalize_kernel(double *__restrict__ out, const double *__restrict__ rs,
+                                      const double *__restrict__ delta, int64_t n, int64_t D) {
+  for (int64_t i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    const double ri = rs[i], di = (double)D * delta[i];
+    const int64_t p0 = pair_index(i, i + 1, n);
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x)
+      out[p0 + (j - i - 1)] = (out[p0 + (j - i - 1)] - di * delta[j]) * (ri * rs[j]);
   }
 }
 
@@ -294,15 +346,44 @@ cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int
   dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
   const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   if (vec4)
-    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32,
-                                                          part);
+    vec_split_kernel<true, false><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32, part, nullptr, 1);
   else
-    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(X, row0, out_row0, n, D, ld, Dp, mu, hi, lo,
-                                                           c32, part);
+    vec_split_kernel<false, false><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32, part, nullptr, 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   vec_finalize_kernel<<<fg, 256, 0, s>>>(part, row0, n, kSplitParts, ss, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_split_slice(const float *X, int64_t row0, int64_t n, int64_t cols,
+                                   int64_t ld, int64_t cols_p, const double *shift,
+                                   __nv_bfloat16 *hi, __nv_bfloat16 *lo, double *part,
+                                   double *part_c, int first_chunk, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
+  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (vec4)
+    vec_split_kernel<true, true><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk);
+  else
+    vec_split_kernel<false, true><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_finalize(const double *part, const double *part_c, int64_t n,
+                                  int64_t D, double *delta, double *ss, double *rs, double *out,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  slice_stats_kernel<<<fg, 256, 0, s>>>(part, part_c, n, kSplitParts, D, delta, ss, rs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n < 2) return e;
+  const int grid = (int)(n - 1 < 65535 ? n - 1 : 65535);
+  slice_finalize_kernel<<<grid, 256, 0, s>>>(out, rs, delta, n, D);
   return cudaGetLastError();
 }
 

@@ -140,3 +140,67 @@ def test_out_of_core_lru_policy(ap, oracle_lib):
     assert np.all(np.abs(r0 - ref) <= tol) and np.all(np.abs(r1 - ref) <= tol)
     assert np.all(cnt == 1)
     assert R1 >= R0 >= 1.0
+
+
+def _slice_cache(n, cols):
+    """Cache for column chunks of `cols` columns with the four-piece ring."""
+    rows = (n + 127) // 128 * 128
+    return cols * (4 * rows + 4 * 256 * min(4, -(-n // 256)))
+
+
+def test_out_of_core_column_slices(ap, oracle_lib):
+    """Column slices (R = 1): rows centred on the mean of their first chunk,
+    the Gram accumulated over three chunks (the last one ragged), the exact
+    centring recovered at the end; large row-dependent means exercise the
+    shifted-data correction."""
+    n, D = 1000, 3000
+    X = synth.vectors_grouped(n, D, seed=41) + torch.linspace(-3.0, 7.0, n)[:, None]
+    X = X.contiguous().pin_memory()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    tol = pearson_tolerance(X.numpy(), pi, pj, 1)
+    cache = max(_slice_cache(n, 1024), 3 * _slot_bytes(D))   # the macro schedule needs 3 slots
+    plan = ap.binding.plan_out_of_core(n, D, cache, ap.binding.AP_OOC_K_SLICED)
+    assert plan["steps"] == 3 and plan["loads"] == 4
+    with ap.Items.from_vectors(X, slot_cache_bytes=cache) as it:
+        r0 = it.run_pairs().cpu().numpy()
+        it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+        r2 = it.run_pairs().cpu().numpy()
+        st = it.stats()
+        again = it.run_pairs().cpu().numpy()
+        cnt = it.run_pairs(ap.AP_FN_COVERAGE).cpu().numpy()
+        assert it.last_device_error() == 0
+        it.set_out_of_core_policy(ap.binding.AP_OOC_RESIDENT_STREAM)
+        r0b = it.run_pairs().cpu().numpy()
+    assert np.all(np.abs(r2 - ref) <= tol), float(np.abs(r2 - ref).max())
+    assert np.all(np.abs(r0 - ref) <= tol)
+    assert st["reuse_R"] == 1.0 and st["h2d_bytes"] == n * D * 4
+    assert np.abs(again - r2).max() <= 1e-12
+    assert np.all(cnt == 1)
+    assert np.abs(r0b - r0).max() <= 1e-12
+    assert np.all(np.abs(r2 - r0) <= regroup_tolerance(X.numpy(), pi, pj) + 2 * tol)
+
+
+@pytest.mark.parametrize("n,D", [(300, 200), (257, 4096)])
+def test_out_of_core_column_slices_shapes(ap, oracle_lib, n, D):
+    X = synth.vectors_grouped(n, D, seed=n + 7).pin_memory()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(X.numpy(), pi, pj)
+    cache = max(_slice_cache(n, 64 * 3), 3 * _slot_bytes(D))
+    with ap.Items.from_vectors(X, slot_cache_bytes=cache) as it:
+        it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+        got = it.run_pairs().cpu().numpy()
+        assert it.last_device_error() == 0
+    assert np.all(np.abs(got - ref) <= pearson_tolerance(X.numpy(), pi, pj, 1))
+
+
+def test_out_of_core_column_slices_reject_small_cache(ap):
+    n, D = 1000, 64
+    X = synth.vectors_grouped(n, D, seed=2).pin_memory()
+    cache = 3 * _slot_bytes(D)               # three macro slots, not 64 columns of all rows
+    assert cache < _slice_cache(n, 64)
+    with ap.Items.from_vectors(X, slot_cache_bytes=cache) as it:
+        with pytest.raises(ap.APError):
+            it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+        r = it.run_pairs().cpu().numpy()     # the macro schedule is untouched
+    assert np.isfinite(r).all()
