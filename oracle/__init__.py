@@ -65,6 +65,11 @@ def _load():
             lib.or_overlap_pairs.restype = None
             lib.or_overlap_pairs.argtypes = [i32, vp, vp, vp, vp, vp, vp, i64, vp, vp,
                                              vp, vp, vp, vp, i32]
+            lib.or_gmm_pairs.restype = None
+            lib.or_gmm_pairs.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp,
+                                         vp, vp, i32]
+            lib.or_gmm_self.restype = None
+            lib.or_gmm_self.argtypes = [i32, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32]
             lib.or_overlap_grad_pairs.restype = None
             lib.or_overlap_grad_pairs.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp,
                                                   vp, vp, i32]
@@ -146,6 +151,51 @@ def overlap(clouds: dict, pi, pj, params=None, n_threads: int | None = None,
     if with_cond:
         return f, kappa, bound
     return f
+
+
+def _cloud_args(clouds):
+    off = _i64(clouds["offsets"])
+    x, y = _f32(clouds["x"]), _f32(clouds["y"])
+    z = _f32(clouds.get("z")) if clouds["dim"] == 3 else None
+    return off, x, y, z, _f32(clouds["sigma"]), _f32(clouds.get("weight"))
+
+
+def _gmm(which, clouds, pi, pj, params, n_threads, with_bound):
+    pi, pj = _i64(pi), _i64(pj)
+    n = len(pi)
+    out = np.empty(n, np.float64)
+    bound = np.empty(n, np.float64) if with_bound else None
+    prm = None if params is None else np.ascontiguousarray(params, np.float64).reshape(-1)
+    off, x, y, z, s, w = _cloud_args(clouds)
+    _load().or_gmm_pairs(which, int(clouds["dim"]), _p(off), _p(x), _p(y), _p(z), _p(s), _p(w),
+                         n, _p(pi), _p(pj), _p(prm), _p(out), _p(bound),
+                         n_threads or default_threads())
+    return (out, bound) if with_bound else out
+
+
+def gmm_l2(clouds: dict, pi, pj, params=None, n_threads: int | None = None,
+           with_bound: bool = False):
+    """Squared L2 distance S_i + S_j - 2 C_ij between the items as Gaussian
+    mixtures (Sec. V-C's first particle score), FP64; pairs may have i == j."""
+    return _gmm(1, clouds, pi, pj, params, n_threads, with_bound)
+
+
+def bhattacharyya(clouds: dict, pi, pj, params=None, n_threads: int | None = None,
+                  with_bound: bool = False):
+    """Bhattacharyya cost sum_ab sqrt(w_a w_b) BC(N_a, N_b) (Sec. V-C's
+    second particle score), FP64."""
+    return _gmm(2, clouds, pi, pj, params, n_threads, with_bound)
+
+
+def gmm_self(clouds: dict, n_threads: int | None = None, with_bound: bool = False):
+    """S_i = integral of p_i^2 for every item, FP64."""
+    off, x, y, z, s, w = _cloud_args(clouds)
+    n = len(off) - 1
+    S = np.empty(n, np.float64)
+    bound = np.empty(n, np.float64) if with_bound else None
+    _load().or_gmm_self(int(clouds["dim"]), _p(off), _p(x), _p(y), _p(z), _p(s), _p(w), n,
+                        _p(S), _p(bound), n_threads or default_threads())
+    return (S, bound) if with_bound else S
 
 
 def overlap_grad(clouds: dict, pi, pj, params=None, n_threads: int | None = None):

@@ -156,6 +156,106 @@ void or_overlap_pairs(int dim, const int64_t *off, const float *x,
   parallel_ranges(overlap_range, &c, n_pairs, n_threads);
 }
 
+/* ------------------------------------------------------------------ */
+/* Particle scores as Gaussian mixtures: GMM L2 distance, Bhattacharyya  */
+/* ------------------------------------------------------------------ */
+
+/* sum over a in item i, b in item j of one score's terms; the transform
+ * (cs, sn, tx, ty) moves item j's points */
+static void gmm_sum(int which, const overlap_ctx *c, int64_t i, int64_t j, double cs,
+                    double sn, double tx, double ty, double *sum, double *bnd) {
+  const double pi_ = 3.14159265358979323846;
+  double acc = 0.0, eb = 0.0;
+  for (int64_t a = c->off[i]; a < c->off[i + 1]; ++a) {
+    double wa = c->w ? (double)c->w[a] : 1.0;
+    double sa = (double)c->sigma[a];
+    for (int64_t b = c->off[j]; b < c->off[j + 1]; ++b) {
+      double wb = c->w ? (double)c->w[b] : 1.0;
+      double sb = (double)c->sigma[b];
+      double xb = (double)c->x[b], yb = (double)c->y[b];
+      double dx = (double)c->x[a] - (cs * xb - sn * yb + tx);
+      double dy = (double)c->y[a] - (sn * xb + cs * yb + ty);
+      double d2 = dx * dx + dy * dy;
+      if (c->dim == 3) {
+        double dz = (double)c->z[a] - (double)c->z[b];
+        d2 += dz * dz;
+      }
+      double s2 = sa * sa + sb * sb, arg, term;
+      if (which == 1) {
+        arg = d2 / (2.0 * s2);
+        term = wa * wb * pow(2.0 * pi_ * s2, -0.5 * c->dim) * exp(-arg);
+      } else {
+        arg = d2 / (4.0 * s2);
+        term = sqrt(wa * wb) * pow(2.0 * sa * sb / s2, 0.5 * c->dim) * exp(-arg);
+      }
+      acc += term;
+      eb += (arg + 6.0) * ldexp(1.0, -23) * fabs(term);
+    }
+  }
+  *sum = acc;
+  *bnd = eb;
+}
+
+typedef struct {
+  overlap_ctx c;
+  int which;
+} gmm_ctx;
+
+static void gmm_range(void *vc, int64_t lo, int64_t hi) {
+  gmm_ctx *g = (gmm_ctx *)vc;
+  const overlap_ctx *c = &g->c;
+  for (int64_t q = lo; q < hi; ++q) {
+    int64_t i = c->pi[q], j = c->pj[q];
+    double th = 0.0, tx = 0.0, ty = 0.0;
+    if (c->params) { th = c->params[3 * q]; tx = c->params[3 * q + 1]; ty = c->params[3 * q + 2]; }
+    double cs = cos(th), sn = sin(th), v, e;
+    gmm_sum(g->which, c, i, j, cs, sn, tx, ty, &v, &e);
+    if (g->which == 1) {
+      double si, ei, sj, ej;
+      gmm_sum(1, c, i, i, 1.0, 0.0, 0.0, 0.0, &si, &ei);
+      gmm_sum(1, c, j, j, 1.0, 0.0, 0.0, 0.0, &sj, &ej);
+      c->f[q] = si + sj - 2.0 * v;
+      if (c->bound) c->bound[q] = ei + ej + 2.0 * e;
+    } else {
+      c->f[q] = v;
+      if (c->bound) c->bound[q] = e;
+    }
+  }
+}
+
+void or_gmm_pairs(int which, int dim, const int64_t *off, const float *x,
+                  const float *y, const float *z, const float *sigma,
+                  const float *w, int64_t n_pairs, const int64_t *pi,
+                  const int64_t *pj, const double *params, double *out,
+                  double *bound, int n_threads) {
+  gmm_ctx g;
+  memset(&g, 0, sizeof g);
+  g.which = which;
+  g.c.dim = dim; g.c.off = off; g.c.x = x; g.c.y = y; g.c.z = z; g.c.sigma = sigma;
+  g.c.w = w; g.c.pi = pi; g.c.pj = pj; g.c.params = params; g.c.f = out; g.c.bound = bound;
+  parallel_ranges(gmm_range, &g, n_pairs, n_threads);
+}
+
+static void gmm_self_range(void *vc, int64_t lo, int64_t hi) {
+  const overlap_ctx *c = (const overlap_ctx *)vc;
+  for (int64_t i = lo; i < hi; ++i) {
+    double v, e;
+    gmm_sum(1, c, i, i, 1.0, 0.0, 0.0, 0.0, &v, &e);
+    c->f[i] = v;
+    if (c->bound) c->bound[i] = e;
+  }
+}
+
+void or_gmm_self(int dim, const int64_t *off, const float *x, const float *y,
+                 const float *z, const float *sigma, const float *w,
+                 int64_t n_items, double *S, double *bound, int n_threads) {
+  overlap_ctx c;
+  memset(&c, 0, sizeof c);
+  c.dim = dim; c.off = off; c.x = x; c.y = y; c.z = z; c.sigma = sigma; c.w = w;
+  c.f = S; c.bound = bound;
+  parallel_ranges(gmm_self_range, &c, n_items, n_threads);
+}
+
 static void overlap_grad_range(void *vc, int64_t lo, int64_t hi) {
   overlap_ctx *c = (overlap_ctx *)vc;
   for (int64_t q = lo; q < hi; ++q) {

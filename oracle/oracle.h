@@ -63,6 +63,38 @@ void or_overlap_pairs(int dim, const int64_t *off, const float *x,
                       double *kappa, double *bound, int n_threads);
 
 /*
+ * The two particle scores of the microscopy application (Sec. V-C names a
+ * quadratic L2 distance between Gaussian mixtures and a Bhattacharyya
+ * distance without writing either down; these are the standard forms).
+ * Component a of item i: weight w_a, density N(x; x_a, sigma_a^2 I) in dim
+ * dimensions; s2 = sigma_a^2 + sigma_b^2, u_b = R(theta) x_b + t as above.
+ *
+ * which == 1, the squared L2 distance between the mixtures:
+ *   d(i,j) = S_i + S_j - 2 C_ij,
+ *   C_ij = integral of p_i p_j = sum_a sum_b w_a w_b (2 pi s2)^(-dim/2)
+ *                                          exp(-|x_a - u_b|^2 / (2 s2)),
+ *   S_i = C_ii at the identity (every a, a' of item i, a = a' included).
+ * which == 2, the Bhattacharyya cost: component pairs weighted by
+ *   sqrt(w_a w_b) times the Bhattacharyya coefficient of the two Gaussians,
+ *   f(i,j) = sum_a sum_b sqrt(w_a w_b) (2 sigma_a sigma_b / s2)^(dim/2)
+ *                                     exp(-|x_a - u_b|^2 / (4 s2)).
+ * Pairs may have i == j.  bound[q] (optional): an absolute error scale for an
+ * FP32 evaluation, the sum over the terms involved (for which == 1 those of
+ * S_i, S_j and twice those of C_ij) of (|arg| + 6) 2^-23 |term|, arg the
+ * exponent's magnitude.
+ */
+void or_gmm_pairs(int which, int dim, const int64_t *off, const float *x,
+                  const float *y, const float *z, const float *sigma,
+                  const float *w, int64_t n_pairs, const int64_t *pi,
+                  const int64_t *pj, const double *params, double *out,
+                  double *bound, int n_threads);
+
+/* S_i of every item (the which == 1 self term) and its error scale */
+void or_gmm_self(int dim, const int64_t *off, const float *x, const float *y,
+                 const float *z, const float *sigma, const float *w,
+                 int64_t n_items, double *S, double *bound, int n_threads);
+
+/*
  * The same cost (dim == 2) and its analytic gradient with respect to
  * (theta, tx, ty).  With y_b = R x_b + t, d = x_a - y_b, s2 = sa^2 + sb^2,
  * e = exp(-|d|^2 / (2 s2)):
