@@ -434,6 +434,9 @@ def run_cloud_workload(args):
     wl = args.workload
     if wl == "overlap2d_n256":
         c = synth.clouds_uniform(n=256, dim=2, size=(64, 128), seed=0)
+    elif wl == "particles2d_n256":
+        # the paper's microscopy set: 256 particles of 1000-2000 localisations
+        c = synth.clouds_uniform(n=256, dim=2, size=(1000, 2000), sigma=(0.01, 0.03), seed=0)
     elif wl == "overlap3d_n20000":
         c = synth.clouds_lognormal(n=args.n or 20000, dim=3, seed=0)
     else:
@@ -454,12 +457,15 @@ def run_cloud_workload(args):
     n_asc = 20
     prm = torch.zeros(P, 3, device="cuda")
 
+    fn = {"overlap": ap.AP_FN_OVERLAP, "gmm_l2": ap.AP_FN_GMM_L2,
+          "bhattacharyya": ap.AP_FN_BHATTACHARYYA}[args.fn]
+
     def step():
         if wl == "register2d_n1024":
             prm.zero_()
             items.ascent(prm, n_asc, 1e-3)
         else:
-            items.run_pairs(ap.AP_FN_OVERLAP, out=out)
+            items.run_pairs(fn, out=out)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -488,6 +494,7 @@ def run_cloud_workload(args):
             "data": "synthetic",
             "config": {"workload": f"overlap3d_n{n}" if wl == "overlap3d_n20000" else wl,
                        "n_items": n, "pairs": P, "point_pairs": point_pairs,
+                       "pair_function": "ascent" if wl == "register2d_n1024" else args.fn,
                        "plan": tuned},
             "point_pairs_per_s": point_pairs * (n_asc if wl == "register2d_n1024" else 1)
             / (ms / 1e3),
@@ -512,10 +519,14 @@ def run_cloud_workload(args):
         t0 = time.perf_counter()
         if wl == "register2d_n1024":
             f_ref, _ = oracle.overlap_grad(c, pi, pj, None, n_threads=cores)
+        elif args.fn == "gmm_l2":
+            f_ref = oracle.gmm_l2(c, pi, pj, n_threads=cores)
+        elif args.fn == "bhattacharyya":
+            f_ref = oracle.bhattacharyya(c, pi, pj, n_threads=cores)
         else:
             f_ref = oracle.overlap(c, pi, pj, n_threads=cores)
         secs = time.perf_counter() - t0
-        items.run_pairs(ap.AP_FN_OVERLAP, out=out)
+        items.run_pairs(ap.AP_FN_OVERLAP if wl == "register2d_n1024" else fn, out=out)
         p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
         got = out[p].double().cpu().numpy()
         line["max_rel_err_sampled"] = float((np.abs(got - f_ref) / np.abs(f_ref)).max())
@@ -531,7 +542,10 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--workload", default="pearson_n8192_d1048576",
                     choices=["pearson_n8192_d1048576", "overlap2d_n256", "overlap3d_n20000",
-                             "register2d_n1024", "pearson_ooc_n8192_d3145728"])
+                             "register2d_n1024", "pearson_ooc_n8192_d3145728",
+                             "particles2d_n256"])
+    ap.add_argument("--fn", default="overlap", choices=["overlap", "gmm_l2", "bhattacharyya"],
+                    help="pair function of the cloud workloads")
     ap.add_argument("--ref-pairs", type=int, default=2000)
     ap.add_argument("--n", type=int, default=0,
                     help="item count override (smaller cases for profiling)")

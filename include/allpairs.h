@@ -62,7 +62,19 @@ typedef enum {
   /* debugging pair function: atomically adds 1 to int32 out[p(i,j)] for every
    * pair the schedule visits (coverage check: every i < j exactly once).
    * Works for any item kind; the caller zeroes out[] first. */
-  AP_FN_COVERAGE = 2
+  AP_FN_COVERAGE = 2,
+  /* the two particle scores of the microscopy application (Sec. V-C names
+   * them; these are their standard forms), items as Gaussian mixtures with
+   * components N(x; x_a, s_a^2 I), weights w_a, s2 = s_a^2 + s_b^2:
+   * squared L2 distance between the mixtures, output float[P]:
+   *   d(i,j) = S_i + S_j - 2 sum_a sum_b w_a w_b (2 pi s2)^(-dim/2)
+   *                                     exp(-|x_a - (R x_b + t)|^2 / (2 s2)),
+   *   S_i the same double sum over item i with itself (a = a' included) */
+  AP_FN_GMM_L2 = 3,
+  /* Bhattacharyya cost, output float[P]:
+   *   f(i,j) = sum_a sum_b sqrt(w_a w_b) (2 s_a s_b / s2)^(dim/2)
+   *                          exp(-|x_a - (R x_b + t)|^2 / (4 s2)) */
+  AP_FN_BHATTACHARYYA = 4
 } ap_pair_fn;
 
 typedef enum {
@@ -172,6 +184,10 @@ ap_status ap_update_items(ap_items *items, const float *data, int32_t data_on_ho
  *   fn = AP_FN_PEARSON: vectors; out double[P]; precision selects the Gram
  *        path (the representation must have been built at creation).
  *   fn = AP_FN_COVERAGE: any kind; out int32[P] is incremented.
+ *   fn = AP_FN_GMM_L2, AP_FN_BHATTACHARYYA: clouds; out float[P]; params as
+ *        for the overlap.  The first call of each builds a re-scaled copy of
+ *        the storage (16 bytes a point, + 4 for 3-D weights) and, for the L2
+ *        distance, the self terms S_i; later calls reuse them.
  * Errors: AP_ERR_INVALID_ARG (fn/kind mismatch, NULL out with P > 0, params
  * with 3-D clouds), AP_ERR_STATE (representation not built), AP_ERR_CUDA,
  * AP_ERR_TIMEOUT.

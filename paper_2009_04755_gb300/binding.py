@@ -21,7 +21,7 @@ AP_OK, AP_ERR_INVALID_ARG, AP_ERR_OOM, AP_ERR_CUDA, AP_ERR_TIMEOUT, AP_ERR_UNSUP
 # ap_item_kind
 AP_ITEMS_CLOUD2D, AP_ITEMS_CLOUD3D, AP_ITEMS_VECTOR = range(3)
 # ap_pair_fn
-AP_FN_OVERLAP, AP_FN_PEARSON, AP_FN_COVERAGE = range(3)
+AP_FN_OVERLAP, AP_FN_PEARSON, AP_FN_COVERAGE, AP_FN_GMM_L2, AP_FN_BHATTACHARYYA = range(5)
 # ap_precision
 AP_PREC_FP32, AP_PREC_SPLIT_BF16 = range(2)
 
@@ -234,7 +234,8 @@ class Items:
         if fn is None:
             fn = AP_FN_PEARSON if self.kind == AP_ITEMS_VECTOR else AP_FN_OVERLAP
         if out is None:
-            dt = {AP_FN_OVERLAP: torch.float32, AP_FN_PEARSON: torch.float64,
+            dt = {AP_FN_OVERLAP: torch.float32, AP_FN_GMM_L2: torch.float32,
+                  AP_FN_BHATTACHARYYA: torch.float32, AP_FN_PEARSON: torch.float64,
                   AP_FN_COVERAGE: torch.int32}[fn]
             out = (torch.zeros if fn == AP_FN_COVERAGE else torch.empty)(
                 max(self.P, 1), dtype=dt, device="cuda")

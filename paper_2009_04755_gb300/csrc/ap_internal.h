@@ -66,6 +66,11 @@ struct CloudStore {
   int32_t *d_tiles = nullptr;       // [n_tiles][2] block pairs (I <= J)
   int64_t n_tiles = 0;
   int64_t tiles_cap = 0;
+  // particle scores: re-scaled storage per score (index score - 1), built on
+  // first use, and the GMM L2 self terms per original item
+  float4 *d_pts_score[2] = {nullptr, nullptr};
+  float *d_lw_score[2] = {nullptr, nullptr};
+  double *d_self = nullptr;
 };
 
 // one macro pair (a <= b) of an out-of-core batch and the slots holding them
@@ -134,7 +139,7 @@ struct VecStore {
 namespace ap {
 // a captured launch sequence, replayed with cudaGraphLaunch
 struct GraphKey {
-  int32_t kind;                    // 1 overlap, 2 coverage, 3 ascent
+  int32_t kind;                    // 1 overlap, 2 coverage, 3 ascent, 4 L2, 5 Bhattacharyya
   const void *a, *b, *c, *d;       // buffers the sequence reads / writes
   float eta, fmin;
   int32_t n;
@@ -267,6 +272,15 @@ cudaError_t launch_overlap_grad_q(const CloudStore &cs, int32_t *queue, const fl
                                   const float *grad_out, float *grad_params, float *f_out,
                                   float eta, float fmin, float *params_io, int32_t *flags,
                                   cudaStream_t s);
+// particle scores (score 1 GMM L2 distance, 2 Bhattacharyya cost) on the
+// re-scaled storage pts / lw; self = the L2 self terms (score 1)
+cudaError_t launch_score(const CloudStore &cs, int score, const float4 *pts, const float *lw,
+                         const double *self, const float *params, float *out, int32_t *queue,
+                         cudaStream_t s);
+cudaError_t launch_cloud_rescore(const CloudStore &cs, int score, float4 *pts_out, float *lw_out,
+                                 cudaStream_t s);
+cudaError_t launch_cloud_self(const CloudStore &cs, const float4 *pts, const float *lw,
+                              double *self, cudaStream_t s);
 constexpr int kOverlapMaxRowJobs = 128;   // chunks of one I block
 constexpr int kOverlapMaxBlockItems = 32;
 cudaError_t launch_cloud_pack(const float *x, const float *y, const float *z,

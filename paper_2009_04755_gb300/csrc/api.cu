@@ -46,6 +46,8 @@ void free_items(ap_items *it) {
   CloudStore &c = it->cl;
   dfree(c.d_pts); dfree(c.d_lw); dfree(c.d_poff); dfree(c.d_cnt); dfree(c.d_perm);
   dfree(c.d_bstart); dfree(c.d_tiles);
+  for (int k = 0; k < 2; ++k) { dfree(c.d_pts_score[k]); dfree(c.d_lw_score[k]); }
+  dfree(c.d_self);
   VecStore &v = it->vec;
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
@@ -405,11 +407,14 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   if (!it) return AP_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = it->kind == AP_ITEMS_VECTOR ? it->vec.n : it->cl.n;
-  if (fn != AP_FN_OVERLAP && fn != AP_FN_PEARSON && fn != AP_FN_COVERAGE) return AP_ERR_INVALID_ARG;
+  if (fn != AP_FN_OVERLAP && fn != AP_FN_PEARSON && fn != AP_FN_COVERAGE && fn != AP_FN_GMM_L2 &&
+      fn != AP_FN_BHATTACHARYYA)
+    return AP_ERR_INVALID_ARG;
   if (precision != AP_PREC_FP32 && precision != AP_PREC_SPLIT_BF16) return AP_ERR_INVALID_ARG;
-  if (fn == AP_FN_OVERLAP && it->kind == AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
+  const bool cloud_fn = fn == AP_FN_OVERLAP || fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA;
+  if (cloud_fn && it->kind == AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
   if (fn == AP_FN_PEARSON && it->kind != AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
-  if (params && (fn != AP_FN_OVERLAP || it->kind != AP_ITEMS_CLOUD2D)) return AP_ERR_INVALID_ARG;
+  if (params && (!cloud_fn || it->kind != AP_ITEMS_CLOUD2D)) return AP_ERR_INVALID_ARG;
   if (n < 2) return AP_OK;
   if (!out) return AP_ERR_INVALID_ARG;
   const int cover = fn == AP_FN_COVERAGE;
@@ -449,6 +454,34 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
       it->stats.tile_n = 128;
     }
     it->stats.item_loads = v.n;
+    it->stats.reuse_R = 1.0;
+    it->stats.slot_hit_rate = 1.0;
+    return AP_OK;
+  }
+  if (fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA) {
+    const int score = fn == AP_FN_GMM_L2 ? 1 : 2;
+    CloudStore &c = it->cl;
+    if (!c.d_pts_score[score - 1]) {
+      // the re-scaled storage (and the L2 self terms) on first use
+      const bool lw = score == 2 ? c.dim == 3 : c.d_lw != nullptr;
+      AP_TRY(dmalloc(&c.d_pts_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
+      if (lw) AP_TRY(dmalloc(&c.d_lw_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
+      AP_TRY(launch_cloud_rescore(c, score, c.d_pts_score[score - 1], c.d_lw_score[score - 1], s));
+      if (score == 1) {
+        AP_TRY(dmalloc(&c.d_self, (size_t)c.n));
+        AP_TRY(launch_cloud_self(c, c.d_pts_score[0], c.d_lw_score[0], c.d_self, s));
+      }
+    }
+    GraphKey key{3 + score, params, out, nullptr, nullptr, 0.f, 0.f, 1};
+    ap_items *h = it;
+    ap_status st = run_graphed(it, key, s, [h, params, out, score](cudaStream_t cs) {
+      const CloudStore &c = h->cl;
+      return launch_score(c, score, c.d_pts_score[score - 1], c.d_lw_score[score - 1], c.d_self,
+                          params, reinterpret_cast<float *>(out), h->d_queue, cs);
+    });
+    if (st != AP_OK) return st;
+    it->stats.tiles = it->cl.n_tiles;
+    it->stats.item_loads = it->cl.n;
     it->stats.reuse_R = 1.0;
     it->stats.slot_hit_rate = 1.0;
     return AP_OK;

@@ -17,6 +17,16 @@
 //   df/dt = 2 ln2 * R sum e r d',   df/dtheta = 2 ln2 * sum e r (x_b d'_y - y_b d'_x)
 // with d' = R^T (x_a - t) - x_b and r = 1 / (s2k_a + s2k_b).
 //
+// The two particle scores of the microscopy application run through the same
+// kernel (SCORE 1, 2) on re-scaled copies of the storage (positive s2k):
+//   SCORE 1, GMM L2 cross term (s2k = 2 ln2 s^2, lw = log2 w):
+//     term = w_a w_b (2 pi s2)^(-d/2) exp(-d^2 / (2 s2)) = C q^d 2^(lw_a + lw_b - d^2 q^2)
+//   SCORE 2, Bhattacharyya (s2k = 4 ln2 s^2, lw = log2 w / 2 + (d/2) log2 sigma):
+//     term = sqrt(w_a w_b) (2 s_a s_b / s2)^(d/2) exp(-d^2 / (4 s2)) = C q^d 2^(...)
+// with q = rsqrt(s2k_a + s2k_b) (one MUFU, as the reciprocal of the overlap)
+// and C = (ln2 / pi)^(d/2) or (8 ln2)^(d/2); the L2 distance adds the per-item
+// self terms S_i + S_j - 2 C sum in the epilogue.
+//
 // Schedule: one persistent CTA per SM slot pops tiles (I block, J block) of
 // the upper triangle of item blocks from an atomic queue (Sec. IV-B).  The J
 // block's points are staged into shared memory with one bulk asynchronous
@@ -44,6 +54,11 @@ enum Mode { FWD = 0, FWD_T = 1, GRAD = 2, COVER = 3 };
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsq_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -90,9 +105,11 @@ struct Params {
   float *params_io;      // ascent: params updated in place
   int32_t *flags;        // ascent: skipped steps
   float eta, fmin;
+  const double *self;    // SCORE 1: S per original item
+  double score_c;        // SCORE 1, 2: the constant C
 };
 
-template <int DIM, bool HAS_W, int MODE, int R>
+template <int DIM, bool HAS_W, int MODE, int R, int SCORE>
 __global__ void __launch_bounds__(kThreads)
 overlap_kernel(Params P) {
   constexpr int NV = (MODE == GRAD) ? 4 : 1;     // partial values per (row job, j)
@@ -227,7 +244,9 @@ overlap_kernel(Params P) {
               if (DIM == 3) { v[h][2] = q.z; v[h][3] = q.w; v[h][4] = HAS_W ? exp2f(__ldg(P.lw + a)) : 1.f; }
               else { v[h][2] = 0.f; v[h][3] = q.z; v[h][4] = exp2f(q.w); }
             } else {
-              v[h][0] = 0.f; v[h][1] = 0.f; v[h][2] = 0.f; v[h][3] = -1.f; v[h][4] = 0.f;
+              // outside the item: weight 0, an s2k of the storage's sign
+              v[h][0] = 0.f; v[h][1] = 0.f; v[h][2] = 0.f; v[h][3] = SCORE ? 1.f : -1.f;
+              v[h][4] = 0.f;
             }
           }
           nax[p] = make_float2(-v[0][0], -v[1][0]);
@@ -291,11 +310,19 @@ overlap_kernel(Params P) {
                   const float2 dz = __fadd2_rn(make_float2(q.z, q.z), naz[p]);
                   d2 = __ffma2_rn(dz, dz, d2);
                 }
-                const float2 ns = __fadd2_rn(nas[p], bs2);           // -(s2k_a + s2k_b)
-                const float2 nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                const float2 ns = __fadd2_rn(nas[p], bs2);   // -(s2k_a + s2k_b); SCORE: +
+                float2 nr, qd = z2;
+                if (SCORE) {
+                  const float2 q = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
+                  nr = __fmul2_rn(q, make_float2(-q.x, -q.y));        // -1 / s2k
+                  qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
+                                : __fmul2_rn(q, make_float2(-nr.x, -nr.y));   // q^d
+                } else {
+                  nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                }
                 const float2 arg = __ffma2_rn(d2, nr, lw2);          // lw_b - d^2 / s2k
                 const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                blF[p] = __fadd2_rn(blF[p], e);
+                blF[p] = SCORE ? __ffma2_rn(e, qd, blF[p]) : __fadd2_rn(blF[p], e);
                 if (MODE == GRAD) {
                   // per a-point sums of -e r, -e r x_b and -e r y_b (e nr = -e r);
                   // the a'-dependent factors are applied once per a-point
@@ -377,7 +404,9 @@ overlap_kernel(Params P) {
         if (MODE == GRAD) { sX += (double)src[1]; sY += (double)src[2]; sT += (double)src[3]; }
       }
       if (MODE == FWD || MODE == FWD_T) {
-        P.out[p] = (float)sF;
+        if (SCORE == 1) P.out[p] = (float)(P.self[oi] + P.self[oj] - 2.0 * P.score_c * sF);
+        else if (SCORE == 2) P.out[p] = (float)(P.score_c * sF);
+        else P.out[p] = (float)sF;
       } else if (MODE == GRAD) {
         // rotate the translation part back: df/dt = 2 ln2 R sum e r d'
         const float *pp = P.params_io ? P.params_io : P.params;
@@ -447,7 +476,78 @@ __global__ void cloud_pack_kernel(const float *__restrict__ x, const float *__re
   }
 }
 
-template <int DIM, bool HAS_W, int MODE>
+// Re-scaled storage of a particle score from the overlap's storage
+// (s2k = -2 ln2 sigma^2, lw = log2 w): SCORE 1 s2k = +2 ln2 sigma^2 with lw
+// unchanged, SCORE 2 s2k = +4 ln2 sigma^2 and lw = lw / 2 + (d/4) log2 sigma^2.
+// Padding keeps a positive s2k and lw = -inf.
+__global__ void cloud_rescore_kernel(const float4 *__restrict__ pts, const float *__restrict__ lw,
+                                     int64_t n_pts, int dim, int score,
+                                     float4 *__restrict__ out_pts, float *__restrict__ out_lw) {
+  const float ln2x2 = 1.3862943611198906f;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pts;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    float4 q = pts[k];
+    const float s2k = dim == 3 ? q.w : q.z;          // -2 ln2 sigma^2 (padding: -1)
+    float l = dim == 3 ? (lw ? lw[k] : 0.f) : q.w;
+    const float t = score == 1 ? -s2k : -2.f * s2k;
+    if (score == 2) l = 0.5f * l + 0.25f * (float)dim * __log2f(-s2k / ln2x2);
+    if (dim == 3) { q.w = t; if (out_lw) out_lw[k] = l; }
+    else { q.z = t; q.w = l; }
+    out_pts[k] = q;
+  }
+}
+
+// S_i = C sum over a, a' in item i of w_a w_a' q^d 2^(-d^2 q^2) (SCORE 1
+// storage), one CTA per item, FP32 blocks of 64 terms folded into FP64.
+template <int DIM, bool HAS_W>
+__global__ void __launch_bounds__(256)
+cloud_self_kernel(const float4 *__restrict__ pts, const float *__restrict__ lw,
+                  const int64_t *__restrict__ poff, const int32_t *__restrict__ cnt,
+                  const int32_t *__restrict__ perm, int64_t n, double c, double *__restrict__ S) {
+  __shared__ double red[8];
+  for (int64_t it = blockIdx.x; it < n; it += gridDim.x) {
+    const int64_t p0 = poff[it];
+    const int m = cnt[it];
+    double acc = 0.0;
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      const float4 qa = pts[p0 + a];
+      const float sa = DIM == 3 ? qa.w : qa.z;
+      const float la = DIM == 3 ? (HAS_W ? lw[p0 + a] : 0.f) : qa.w;
+      float part = 0.f;
+      for (int b = 0; b < m; ++b) {
+        const float4 qb = pts[p0 + b];
+        const float dx = qb.x - qa.x, dy = qb.y - qa.y;
+        float d2 = fmaf(dx, dx, dy * dy);
+        float sb, lb;
+        if (DIM == 3) {
+          const float dz = qb.z - qa.z;
+          d2 = fmaf(dz, dz, d2);
+          sb = qb.w;
+          lb = HAS_W ? lw[p0 + b] : 0.f;
+        } else {
+          sb = qb.z;
+          lb = qb.w;
+        }
+        const float q = rsq_approx(sa + sb), r = q * q;
+        const float e = ex2_approx(fmaf(-d2, r, la + lb));
+        part = fmaf(e, DIM == 2 ? r : r * q, part);
+        if ((b & 63) == 63) { acc += (double)part; part = 0.f; }
+      }
+      acc += (double)part;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+      S[perm[it]] = c * tot;
+    }
+    __syncthreads();
+  }
+}
+
+template <int DIM, bool HAS_W, int MODE, int SCORE = 0>
 cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s) {
   constexpr int NV = (MODE == GRAD) ? 4 : 1;
   size_t smem = (size_t)P.stage_cap * 16 + ((DIM == 3 && HAS_W) ? (size_t)P.stage_cap * 4 : 0) +
@@ -455,8 +555,8 @@ cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s)
                 (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
   void (*kern)(Params) = nullptr;
   switch (reg_r) {
-    case 2: kern = overlap_kernel<DIM, HAS_W, MODE, 2>; break;
-    default: kern = overlap_kernel<DIM, HAS_W, MODE, 4>; break;
+    case 2: kern = overlap_kernel<DIM, HAS_W, MODE, 2, SCORE>; break;
+    default: kern = overlap_kernel<DIM, HAS_W, MODE, 4, SCORE>; break;
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -508,6 +608,53 @@ cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out
   if (params) return launch_r<2, true, FWD_T>(cs, P, cs.reg_r, s);
   if (cs.dim == 3) return w3 ? launch_r<3, true, FWD>(cs, P, cs.reg_r, s) : launch_r<3, false, FWD>(cs, P, cs.reg_r, s);
   return launch_r<2, true, FWD>(cs, P, cs.reg_r, s);
+}
+
+cudaError_t launch_score(const CloudStore &cs, int score, const float4 *pts, const float *lw,
+                         const double *self, const float *params, float *out, int32_t *queue,
+                         cudaStream_t s) {
+  if (cs.n_tiles <= 0) return cudaSuccess;
+  Params P = base_params(cs, queue, status_of(queue));
+  P.pts = pts;
+  P.lw = lw;
+  P.out = out;
+  P.params = params;
+  P.self = self;
+  P.score_c = score == 1 ? pow(0.6931471805599453 / 3.141592653589793, 0.5 * cs.dim)
+                         : pow(8.0 * 0.6931471805599453, 0.5 * cs.dim);
+  const bool w3 = (cs.dim == 3) && lw != nullptr;
+  if (score == 1) {
+    if (params) return launch_r<2, true, FWD_T, 1>(cs, P, cs.reg_r, s);
+    if (cs.dim == 3) return w3 ? launch_r<3, true, FWD, 1>(cs, P, cs.reg_r, s)
+                               : launch_r<3, false, FWD, 1>(cs, P, cs.reg_r, s);
+    return launch_r<2, true, FWD, 1>(cs, P, cs.reg_r, s);
+  }
+  if (params) return launch_r<2, true, FWD_T, 2>(cs, P, cs.reg_r, s);
+  if (cs.dim == 3) return launch_r<3, true, FWD, 2>(cs, P, cs.reg_r, s);
+  return launch_r<2, true, FWD, 2>(cs, P, cs.reg_r, s);
+}
+
+cudaError_t launch_cloud_rescore(const CloudStore &cs, int score, float4 *pts_out, float *lw_out,
+                                 cudaStream_t s) {
+  if (cs.total_pts <= 0) return cudaSuccess;
+  const int64_t blocks = (cs.total_pts + 255) / 256;
+  cloud_rescore_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(
+      cs.d_pts, cs.d_lw, cs.total_pts, cs.dim, score, pts_out, lw_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cloud_self(const CloudStore &cs, const float4 *pts, const float *lw,
+                              double *self, cudaStream_t s) {
+  if (cs.n <= 0) return cudaSuccess;
+  const double c = pow(0.6931471805599453 / 3.141592653589793, 0.5 * cs.dim);
+  const int grid = (int)(cs.n < 65535 ? cs.n : 65535);
+  if (cs.dim == 3) {
+    if (lw) cloud_self_kernel<3, true><<<grid, 256, 0, s>>>(pts, lw, cs.d_poff, cs.d_cnt, cs.d_perm, cs.n, c, self);
+    else cloud_self_kernel<3, false><<<grid, 256, 0, s>>>(pts, lw, cs.d_poff, cs.d_cnt, cs.d_perm, cs.n, c, self);
+  } else {
+    cloud_self_kernel<2, true><<<grid, 256, 0, s>>>(pts, lw, cs.d_poff, cs.d_cnt, cs.d_perm, cs.n, c, self);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_overlap_grad_q(const CloudStore &cs, int32_t *queue, const float *params,
