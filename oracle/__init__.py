@@ -70,6 +70,8 @@ def _load():
                                          vp, vp, i32]
             lib.or_gmm_self.restype = None
             lib.or_gmm_self.argtypes = [i32, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32]
+            lib.or_sparse_cosine_pairs.restype = None
+            lib.or_sparse_cosine_pairs.argtypes = [vp, vp, vp, i64, vp, vp, vp, i32]
             lib.or_overlap_grad_pairs.restype = None
             lib.or_overlap_grad_pairs.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp,
                                                   vp, vp, i32]
@@ -196,6 +198,19 @@ def gmm_self(clouds: dict, n_threads: int | None = None, with_bound: bool = Fals
     _load().or_gmm_self(int(clouds["dim"]), _p(off), _p(x), _p(y), _p(z), _p(s), _p(w), n,
                         _p(S), _p(bound), n_threads or default_threads())
     return (S, bound) if with_bound else S
+
+
+def sparse_cosine(off, idx, val, pi, pj, n_threads: int | None = None):
+    """Cosine of sparse rows (CSR: off int64 [n+1], idx int32 sorted per row,
+    val float32) per listed pair, FP64, by merging the index lists."""
+    pi, pj = _i64(pi), _i64(pj)
+    c = np.empty(len(pi), np.float64)
+    off = _i64(off)
+    idx = np.ascontiguousarray(idx, np.int32)
+    val = _f32(val)
+    _load().or_sparse_cosine_pairs(_p(off), _p(idx), _p(val), len(pi), _p(pi), _p(pj), _p(c),
+                                   n_threads or default_threads())
+    return c
 
 
 def overlap_grad(clouds: dict, pi, pj, params=None, n_threads: int | None = None):

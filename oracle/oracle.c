@@ -256,6 +256,48 @@ void or_gmm_self(int dim, const int64_t *off, const float *x, const float *y,
   parallel_ranges(gmm_self_range, &c, n_items, n_threads);
 }
 
+/* ------------------------------------------------------------------ */
+/* Cosine of sparse composition vectors (Sec. V-B)                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const int64_t *off;
+  const int32_t *idx;
+  const float *val;
+  const int64_t *pi, *pj;
+  double *c;
+} sparse_ctx;
+
+static double sparse_norm2(const sparse_ctx *s, int64_t i) {
+  double t = 0.0;
+  for (int64_t e = s->off[i]; e < s->off[i + 1]; ++e) t += (double)s->val[e] * (double)s->val[e];
+  return t;
+}
+
+static void sparse_range(void *vc, int64_t lo, int64_t hi) {
+  sparse_ctx *s = (sparse_ctx *)vc;
+  for (int64_t q = lo; q < hi; ++q) {
+    int64_t i = s->pi[q], j = s->pj[q];
+    int64_t a = s->off[i], ae = s->off[i + 1], b = s->off[j], be = s->off[j + 1];
+    double dot = 0.0;
+    while (a < ae && b < be) {          /* merge of the two sorted index lists */
+      if (s->idx[a] < s->idx[b]) ++a;
+      else if (s->idx[a] > s->idx[b]) ++b;
+      else { dot += (double)s->val[a] * (double)s->val[b]; ++a; ++b; }
+    }
+    double ni = sparse_norm2(s, i), nj = sparse_norm2(s, j);
+    s->c[q] = (ni > 0.0 && nj > 0.0) ? dot / sqrt(ni * nj) : NAN;
+  }
+}
+
+void or_sparse_cosine_pairs(const int64_t *off, const int32_t *idx, const float *val,
+                            int64_t n_pairs, const int64_t *pi, const int64_t *pj,
+                            double *c, int n_threads) {
+  sparse_ctx s;
+  s.off = off; s.idx = idx; s.val = val; s.pi = pi; s.pj = pj; s.c = c;
+  parallel_ranges(sparse_range, &s, n_pairs, n_threads);
+}
+
 static void overlap_grad_range(void *vc, int64_t lo, int64_t hi) {
   overlap_ctx *c = (overlap_ctx *)vc;
   for (int64_t q = lo; q < hi; ++q) {

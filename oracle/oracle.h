@@ -95,6 +95,18 @@ void or_gmm_self(int dim, const int64_t *off, const float *x, const float *y,
                  int64_t n_items, double *S, double *bound, int n_threads);
 
 /*
+ * Cosine of sparse composition vectors (the bioinformatics comparison of
+ * Sec. V-B: "essentially the dot product between two sparse vectors"):
+ *   c(i,j) = sum_k a_ik a_jk / sqrt(sum_k a_ik^2 sum_k a_jk^2),
+ * rows in CSR form: entries [off[i], off[i+1]) with strictly increasing
+ * indices idx[] and values val[].  The dot product is a merge of the two
+ * sorted index lists; NaN when a row has no entries or only zeros.
+ */
+void or_sparse_cosine_pairs(const int64_t *off, const int32_t *idx, const float *val,
+                            int64_t n_pairs, const int64_t *pi, const int64_t *pj,
+                            double *c, int n_threads);
+
+/*
  * The same cost (dim == 2) and its analytic gradient with respect to
  * (theta, tx, ty).  With y_b = R x_b + t, d = x_a - y_b, s2 = sa^2 + sb^2,
  * e = exp(-|d|^2 / (2 s2)):

@@ -126,6 +126,47 @@ def vectors_grouped(n: int, D: int, group: int = 16, shared_weight: float = 0.05
     return X
 
 
+def sparse_cv(n: int, dim: int = 20 ** 6, nnz=(100_000, 1_800_000), common: int = 4_000_000,
+              common_boost: float = 8.0, shared_weight: float = 0.6, seed: int = 0,
+              device="cpu", sizes=None):
+    """Synthetic composition vectors (the bioinformatics workload's shape):
+    sparse rows over a k-mer index space of ``dim`` codes (20^6 for k = 6),
+    nnz_i ~ U[nnz[0], nnz[1]] (or ``sizes``), indices drawn per code with a
+    probability ``common_boost`` times higher in the first ``common`` codes
+    (frequent k-mers shared by most species), values v = shared_weight *
+    g[code] + N(0, 1) with one global g ~ N(0, 1), so rows correlate on the
+    codes they share.  Returns (offsets int64 [n+1], indices int32 [nnz]
+    sorted per row, values float32 [nnz]) as numpy arrays; the draws run on
+    ``device`` with torch's seeded generator."""
+    import torch
+
+    rng = _rng(seed + 15485863)
+    if sizes is None:
+        sizes = rng.integers(nnz[0], nnz[1] + 1, size=n)
+    sizes = np.asarray(sizes, np.int64)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    common = min(common, dim)
+    w_common = common_boost
+    w_rest = (dim - common * common_boost / 1.0) / max(dim - common, 1) if dim > common else 0.0
+    w_rest = max(w_rest, 0.05)
+    g = torch.randn(dim, generator=gen, device=device, dtype=torch.float32)
+    off = np.zeros(n + 1, np.int64)
+    idx_parts, val_parts = [], []
+    for i in range(n):
+        p = float(sizes[i]) / dim
+        u = torch.rand(dim, generator=gen, device=device)
+        thr = torch.full((dim,), p * w_rest, device=device)
+        thr[:common] = min(1.0, p * w_common)
+        ids = torch.nonzero(u < thr).flatten()
+        vals = shared_weight * g[ids] + torch.randn(len(ids), generator=gen, device=device)
+        idx_parts.append(ids.to(torch.int32).cpu().numpy())
+        val_parts.append(vals.float().cpu().numpy())
+        off[i + 1] = off[i] + len(ids)
+    return (off, np.concatenate(idx_parts) if n else np.zeros(0, np.int32),
+            np.concatenate(val_parts) if n else np.zeros(0, np.float32))
+
+
 # Workload shapes (seed 0 unless stated)
 WORKLOADS = {
     "overlap2d_n256": dict(kind="clouds_uniform", n=256, dim=2, size=(64, 128),
