@@ -46,7 +46,9 @@ typedef enum {
 typedef enum {
   AP_ITEMS_CLOUD2D = 0,    /* weighted 2-D point clouds (microscopy particles, Sec. V-C) */
   AP_ITEMS_CLOUD3D = 1,    /* weighted 3-D point clouds */
-  AP_ITEMS_VECTOR = 2      /* dense FP32 vectors of one length (noise patterns, Sec. V-A) */
+  AP_ITEMS_VECTOR = 2,     /* dense FP32 vectors of one length (noise patterns, Sec. V-A) */
+  AP_ITEMS_SPARSE = 3      /* sparse FP32 vectors over one index space (composition
+                              vectors, Sec. V-B) */
 } ap_item_kind;
 
 typedef enum {
@@ -74,7 +76,13 @@ typedef enum {
   /* Bhattacharyya cost, output float[P]:
    *   f(i,j) = sum_a sum_b sqrt(w_a w_b) (2 s_a s_b / s2)^(dim/2)
    *                          exp(-|x_a - (R x_b + t)|^2 / (4 s2)) */
-  AP_FN_BHATTACHARYYA = 4
+  AP_FN_BHATTACHARYYA = 4,
+  /* cosine of sparse vectors (the composition-vector comparison of Sec. V-B,
+   * "essentially the dot product between two sparse vectors"):
+   *   c(i,j) = sum_k a_ik a_jk / sqrt(sum_k a_ik^2 sum_k a_jk^2)
+   * FP32 products, FP64 sums and scaling; NaN for a row without non-zero
+   * values; output double[P] */
+  AP_FN_COSINE = 5
 } ap_pair_fn;
 
 typedef enum {
@@ -113,6 +121,12 @@ typedef struct ap_items_desc {
    * and streams items through an HBM slot cache of at most this many bytes
    * (the first-level device cache of Sec. IV-A). */
   uint64_t slot_cache_bytes;
+  /* Sparse vectors (kind SPARSE), CSR: offsets (as above, a host pointer,
+   * int64[n_items + 1]) delimit row i's entries; indices int32[offsets[n]]
+   * strictly increasing within a row and in [0, dim); data float[offsets[n]]
+   * the values.  indices and data are host or device pointers (data_on_host);
+   * dim is the size of the index space (20^k for k-mers of k amino acids). */
+  const int32_t *indices;
 } ap_items_desc;
 
 /* Run statistics of the last ap_run_pairs on a handle. */
@@ -158,10 +172,13 @@ typedef struct ap_plan {
  *   Vectors: per item mu_i and ss_i in FP64 (two passes), then the centred
  *   rows c = x - mu_i, stored as BF16 hi = rn(c), lo = rn(c - hi) for
  *   split-BF16 and/or as FP32 c for the FP32 path, rows padded with zeros.
+ *   Sparse vectors: the CSR arrays copied, FP64 squared norms per row, and
+ *   per column chunk of 2048 codes the first entry of every row in it.
  * Inputs may be freed when the call returns (after a stream synchronise),
  * except the out-of-core host source (see slot_cache_bytes).
  * Errors: AP_ERR_INVALID_ARG (desc/out NULL, negative sizes, bad kind,
- * offsets not non-decreasing, missing arrays), AP_ERR_OOM, AP_ERR_CUDA.
+ * offsets not non-decreasing, missing arrays, sparse indices not strictly
+ * increasing within a row or outside [0, dim)), AP_ERR_OOM, AP_ERR_CUDA.
  * On error *out is set to NULL and nothing is leaked.
  */
 ap_status ap_create_items(const ap_items_desc *desc, void *stream, ap_items **out);
@@ -184,6 +201,7 @@ ap_status ap_update_items(ap_items *items, const float *data, int32_t data_on_ho
  *   fn = AP_FN_PEARSON: vectors; out double[P]; precision selects the Gram
  *        path (the representation must have been built at creation).
  *   fn = AP_FN_COVERAGE: any kind; out int32[P] is incremented.
+ *   fn = AP_FN_COSINE: sparse vectors; out double[P].
  *   fn = AP_FN_GMM_L2, AP_FN_BHATTACHARYYA: clouds; out float[P]; params as
  *        for the overlap.  The first call of each builds a re-scaled copy of
  *        the storage (16 bytes a point, + 4 for 3-D weights) and, for the L2

@@ -7,7 +7,8 @@ The compute path is the CUDA library ``libap.so`` (C ABI in
 * ``autograd`` -- ``OverlapAlign``, a torch.autograd.Function over the overlap
   cost and its hand-written adjoint.
 """
-from .binding import (AP_FN_BHATTACHARYYA, AP_FN_COVERAGE, AP_FN_GMM_L2,  # noqa: F401
+from .binding import (AP_FN_BHATTACHARYYA, AP_FN_COSINE, AP_FN_COVERAGE,  # noqa: F401
+                      AP_FN_GMM_L2,
                       AP_FN_OVERLAP, AP_FN_PEARSON, AP_PREC_FP32,
                       AP_PREC_SPLIT_BF16, APError, Items, lib, pair_count, pair_index,
                       plan_tiles)

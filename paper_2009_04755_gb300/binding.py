@@ -19,9 +19,10 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "allpairs.h")
 AP_OK, AP_ERR_INVALID_ARG, AP_ERR_OOM, AP_ERR_CUDA, AP_ERR_TIMEOUT, AP_ERR_UNSUPPORTED, \
     AP_ERR_STATE = range(7)
 # ap_item_kind
-AP_ITEMS_CLOUD2D, AP_ITEMS_CLOUD3D, AP_ITEMS_VECTOR = range(3)
+AP_ITEMS_CLOUD2D, AP_ITEMS_CLOUD3D, AP_ITEMS_VECTOR, AP_ITEMS_SPARSE = range(4)
 # ap_pair_fn
-AP_FN_OVERLAP, AP_FN_PEARSON, AP_FN_COVERAGE, AP_FN_GMM_L2, AP_FN_BHATTACHARYYA = range(5)
+AP_FN_OVERLAP, AP_FN_PEARSON, AP_FN_COVERAGE, AP_FN_GMM_L2, AP_FN_BHATTACHARYYA, \
+    AP_FN_COSINE = range(6)
 # ap_precision
 AP_PREC_FP32, AP_PREC_SPLIT_BF16 = range(2)
 
@@ -32,7 +33,8 @@ class ItemsDesc(ctypes.Structure):
                 ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("weight", ctypes.c_void_p),
                 ("data", ctypes.c_void_p), ("dim", ctypes.c_int64), ("ld", ctypes.c_int64),
-                ("precisions", ctypes.c_uint32), ("slot_cache_bytes", ctypes.c_uint64)]
+                ("precisions", ctypes.c_uint32), ("slot_cache_bytes", ctypes.c_uint64),
+                ("indices", ctypes.c_void_p)]
 
 
 class RunStats(ctypes.Structure):
@@ -223,6 +225,35 @@ class Items:
             obj._keep.append(X)          # the library reads it on every run
         return obj
 
+    @classmethod
+    def from_sparse(cls, offsets, indices, values, dim: int, stream=None) -> "Items":
+        """Sparse rows in CSR form: offsets int64 [n+1] (host), indices int32
+        (strictly increasing per row, < dim) and values float32 as numpy arrays
+        (copied from the host) or torch tensors (host or GPU)."""
+        import numpy as np
+        import torch
+        off = np.ascontiguousarray(np.asarray(offsets), dtype=np.int64)
+        n = len(off) - 1
+
+        def arr(a, dt):
+            t = a if torch.is_tensor(a) else torch.from_numpy(np.ascontiguousarray(a))
+            return t.to(dtype=dt).contiguous()
+
+        idx, val = arr(indices, torch.int32), arr(values, torch.float32)
+        d = ItemsDesc()
+        d.kind = AP_ITEMS_SPARSE
+        d.data_on_host = 0 if idx.is_cuda else 1
+        assert idx.is_cuda == val.is_cuda
+        d.n_items = n
+        d.offsets = off.ctypes.data
+        d.indices = idx.data_ptr() if idx.numel() else None
+        d.data = val.data_ptr() if val.numel() else None
+        d.dim = int(dim)
+        h = ctypes.c_void_p()
+        check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
+              "ap_create_items")
+        return cls(h, AP_ITEMS_SPARSE, n)
+
     def update(self, X, stream=None):
         check(lib().ap_update_items(self._h, _ptr(X), 0 if X.is_cuda else 1, _stream_ptr(stream)),
               "ap_update_items")
@@ -232,10 +263,12 @@ class Items:
                   out=None, stream=None):
         import torch
         if fn is None:
-            fn = AP_FN_PEARSON if self.kind == AP_ITEMS_VECTOR else AP_FN_OVERLAP
+            fn = {AP_ITEMS_VECTOR: AP_FN_PEARSON, AP_ITEMS_SPARSE: AP_FN_COSINE}.get(
+                self.kind, AP_FN_OVERLAP)
         if out is None:
             dt = {AP_FN_OVERLAP: torch.float32, AP_FN_GMM_L2: torch.float32,
                   AP_FN_BHATTACHARYYA: torch.float32, AP_FN_PEARSON: torch.float64,
+                  AP_FN_COSINE: torch.float64,
                   AP_FN_COVERAGE: torch.int32}[fn]
             out = (torch.zeros if fn == AP_FN_COVERAGE else torch.empty)(
                 max(self.P, 1), dtype=dt, device="cuda")

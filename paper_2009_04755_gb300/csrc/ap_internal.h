@@ -155,11 +155,31 @@ struct GraphEntry {
 };
 }  // namespace ap
 
+namespace ap {
+// sparse vectors in CSR form over an index space of `dim` codes, cut into
+// chunks of kSparseChunk codes; cptr[c][i] = first entry of row i with a
+// code >= c * kSparseChunk, relative to the row's start (chunk-major, so the
+// bounds of 32 consecutive rows in one chunk are one coalesced load)
+constexpr int kSparseChunk = 2048;
+constexpr int kSparseBlock = 32;
+struct SparseStore {
+  int64_t n = 0, dim = 0, nnz = 0, n_chunks = 0;
+  int64_t *d_off = nullptr;
+  int32_t *d_idx = nullptr;
+  float *d_val = nullptr;
+  int32_t *d_cptr = nullptr;        // [n_chunks + 1][n]
+  double *d_rs = nullptr;           // 1 / sqrt(sum of squares), NaN for none
+  int32_t *d_tiles = nullptr;       // block pairs (I <= J) of 32 items
+  int64_t n_tiles = 0;
+};
+}  // namespace ap
+
 struct ap_items {
   int32_t kind = 0;
   int device = 0;
   ap::CloudStore cl;
   ap::VecStore vec;
+  ap::SparseStore sp;
   int32_t *d_status = nullptr;      // [0] device error code, [1..] scratch
   int32_t *d_queue = nullptr;       // tile-queue heads (one per launch slot)
   float *d_scratch = nullptr;       // generic scratch
@@ -281,6 +301,11 @@ cudaError_t launch_cloud_rescore(const CloudStore &cs, int score, float4 *pts_ou
                                  cudaStream_t s);
 cudaError_t launch_cloud_self(const CloudStore &cs, const float4 *pts, const float *lw,
                               double *self, cudaStream_t s);
+// sparse vectors (sparse.cu)
+ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s);
+void free_sparse(SparseStore &sp);
+cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverage,
+                                 int32_t *queue, cudaStream_t s);
 constexpr int kOverlapMaxRowJobs = 128;   // chunks of one I block
 constexpr int kOverlapMaxBlockItems = 32;
 cudaError_t launch_cloud_pack(const float *x, const float *y, const float *z,

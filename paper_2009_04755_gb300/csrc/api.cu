@@ -53,6 +53,7 @@ void free_items(ap_items *it) {
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
   dfree(v.d_panel_units);
   free_out_of_core(v);
+  free_sparse(it->sp);
   free_tc_tensor_maps(v.tmap_hi, v.tmap_lo);
   v.tmap_hi = v.tmap_lo = nullptr;
   dfree(it->d_queue);
@@ -359,7 +360,7 @@ ap_status ap_create_items(const ap_items_desc *desc, void *stream, ap_items **ou
   *out = nullptr;
   if (!desc || desc->n_items < 0) return AP_ERR_INVALID_ARG;
   if (desc->kind != AP_ITEMS_CLOUD2D && desc->kind != AP_ITEMS_CLOUD3D &&
-      desc->kind != AP_ITEMS_VECTOR)
+      desc->kind != AP_ITEMS_VECTOR && desc->kind != AP_ITEMS_SPARSE)
     return AP_ERR_INVALID_ARG;
   if (desc->n_items > INT32_MAX / 4) return AP_ERR_UNSUPPORTED;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -378,6 +379,7 @@ ap_status ap_create_items(const ap_items_desc *desc, void *stream, ap_items **ou
   if (st == AP_OK) {
     it->d_status = it->d_queue + 1;
     if (desc->kind == AP_ITEMS_VECTOR) st = create_vectors(desc, it, s);
+    else if (desc->kind == AP_ITEMS_SPARSE) st = create_sparse(desc, it, s);
     else st = create_clouds(desc, it, s);
   }
   if (st != AP_OK) {
@@ -406,9 +408,13 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
                        void *out, void *stream) {
   if (!it) return AP_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int64_t n = it->kind == AP_ITEMS_VECTOR ? it->vec.n : it->cl.n;
+  const int64_t n = it->kind == AP_ITEMS_VECTOR   ? it->vec.n
+                    : it->kind == AP_ITEMS_SPARSE ? it->sp.n
+                                                  : it->cl.n;
   if (fn != AP_FN_OVERLAP && fn != AP_FN_PEARSON && fn != AP_FN_COVERAGE && fn != AP_FN_GMM_L2 &&
-      fn != AP_FN_BHATTACHARYYA)
+      fn != AP_FN_BHATTACHARYYA && fn != AP_FN_COSINE)
+    return AP_ERR_INVALID_ARG;
+  if ((fn == AP_FN_COSINE) != (it->kind == AP_ITEMS_SPARSE) && fn != AP_FN_COVERAGE)
     return AP_ERR_INVALID_ARG;
   if (precision != AP_PREC_FP32 && precision != AP_PREC_SPLIT_BF16) return AP_ERR_INVALID_ARG;
   const bool cloud_fn = fn == AP_FN_OVERLAP || fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA;
@@ -418,6 +424,15 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   if (n < 2) return AP_OK;
   if (!out) return AP_ERR_INVALID_ARG;
   const int cover = fn == AP_FN_COVERAGE;
+  if (it->kind == AP_ITEMS_SPARSE) {
+    AP_TRY(launch_sparse_cosine(it->sp, reinterpret_cast<double *>(out), cover, it->d_queue, s));
+    it->stats.tiles = it->sp.n_tiles;
+    it->stats.tile_m = it->stats.tile_n = kSparseBlock;
+    it->stats.item_loads = it->sp.n;
+    it->stats.reuse_R = 1.0;
+    it->stats.slot_hit_rate = 1.0;
+    return AP_OK;
+  }
   if (it->kind == AP_ITEMS_VECTOR && it->vec.out_of_core) {
     if (!cover && precision != AP_PREC_SPLIT_BF16) return AP_ERR_STATE;
     return run_out_of_core(it, out, cover, s);

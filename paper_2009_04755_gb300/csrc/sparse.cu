@@ -1,0 +1,264 @@
+// sparse.cu -- cosine of sparse composition vectors, the comparison of the
+// bioinformatics application (Sec. V-B: "essentially the dot product between
+// two sparse vectors"):
+//
+//   c(i,j) = sum_k a_ik a_jk / sqrt(sum_k a_ik^2 sum_k a_jk^2)
+//
+// Rows are CSR (strictly increasing int32 codes, FP32 values) over an index
+// space of `dim` codes (20^k k-mers), cut into chunks of kSparseChunk codes.
+// Schedule: persistent CTAs pop tiles (a block of 32 items I x a block of 32
+// items J, upper triangle in recursive quadrant order, Sec. IV-B) from an
+// atomic queue.  Each of the 16 warps owns one row i of I at a time and a
+// private dense array of one chunk in shared memory: per chunk it scatters
+// row i's entries into the array, then every lane walks its share of the
+// chunk's entries of each of the 32 rows j of J, gathering a_ik from the
+// array -- a dot product costs one shared-memory gather and one 8-byte entry
+// read per entry of row j, and row i's scatter is shared by the 32 rows j.
+// Per lane and row j the FP32 products are summed over up to 64 chunks and
+// then folded into FP64 (per pair, in shared memory); no CTA-wide barrier
+// runs inside the chunk loop.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = 32 * kWarps;
+constexpr int B = kSparseBlock;
+constexpr int W = kSparseChunk;
+constexpr int kFoldChunks = 64;
+
+// entries [lo, hi) of row `row` in chunk c, from the chunk-major pointers
+__device__ __forceinline__ void row_chunk(const int32_t *__restrict__ cptr, int64_t n,
+                                          const int64_t *__restrict__ off, int64_t row, int64_t c,
+                                          int64_t *lo, int64_t *hi) {
+  const int64_t base = off[row];
+  *lo = base + cptr[c * n + row];
+  *hi = base + cptr[(c + 1) * n + row];
+}
+
+template <int COVER>
+__global__ void __launch_bounds__(kThreads, 1)
+sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                  const float *__restrict__ val, const int32_t *__restrict__ cptr,
+                  const double *__restrict__ rs, int64_t n, int64_t n_chunks,
+                  const int32_t *__restrict__ tiles, int64_t n_tiles, int32_t *queue,
+                  void *out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  float *dense_all = reinterpret_cast<float *>(smem);                 // [kWarps][W]
+  double *s_g = reinterpret_cast<double *>(dense_all + kWarps * W);   // [B][B]
+  __shared__ int s_tile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *dense = dense_all + warp * W;
+  for (int k = lane; k < W; k += 32) dense[k] = 0.f;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t >= n_tiles) break;
+    const int64_t I = tiles[2 * t], J = tiles[2 * t + 1];
+    const int64_t i0 = I * B, j0 = J * B;
+    const bool diag = I == J;
+    for (int q = threadIdx.x; q < B * B; q += kThreads) s_g[q] = 0.0;
+    __syncthreads();
+
+    if (!COVER) {
+      // the J block's row starts: lane l holds row j0 + l
+      const int64_t jrow = j0 + lane;
+      const bool jvalid = jrow < n;
+      const int64_t jbase = jvalid ? off[jrow] : 0;
+      for (int il = warp; il < B; il += kWarps) {
+        const int64_t i = i0 + il;
+        if (i >= n) break;
+        float acc[B];
+#pragma unroll
+        for (int jj = 0; jj < B; ++jj) acc[jj] = 0.f;
+        int since = 0;
+        for (int64_t c = 0; c < n_chunks; ++c) {
+          int64_t a0, a1;
+          row_chunk(cptr, n, off, i, c, &a0, &a1);
+          if (a0 == a1) continue;                    // nothing of row i here
+          const int32_t code0 = (int32_t)(c * W);
+          for (int64_t e = a0 + lane; e < a1; e += 32) dense[__ldg(idx + e) - code0] = __ldg(val + e);
+          // bounds of the 32 rows j in this chunk (one coalesced load each)
+          int32_t jlo = 0, jhi = 0;
+          if (jvalid) {
+            jlo = __ldg(cptr + c * n + jrow);
+            jhi = __ldg(cptr + (c + 1) * n + jrow);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int jj = 0; jj < B; ++jj) {
+            const int32_t lo = __shfl_sync(0xffffffffu, jlo, jj);
+            const int32_t hi = __shfl_sync(0xffffffffu, jhi, jj);
+            const int64_t jb = __shfl_sync(0xffffffffu, jbase, jj);
+            if (diag && jj <= il) continue;          // i < j only
+            for (int32_t e = lo + lane; e < hi; e += 32)
+              acc[jj] = fmaf(dense[__ldg(idx + jb + e) - code0], __ldg(val + jb + e), acc[jj]);
+          }
+          __syncwarp();
+          for (int64_t e = a0 + lane; e < a1; e += 32) dense[__ldg(idx + e) - code0] = 0.f;
+          __syncwarp();
+          if (++since == kFoldChunks) {
+            since = 0;
+#pragma unroll
+            for (int jj = 0; jj < B; ++jj) {
+              double v = (double)acc[jj];
+              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+              if (lane == 0) s_g[il * B + jj] += v;
+              acc[jj] = 0.f;
+            }
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < B; ++jj) {
+          double v = (double)acc[jj];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) s_g[il * B + jj] += v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < B * B; q += kThreads) {
+      const int il = q / B, jl = q - il * B;
+      const int64_t i = i0 + il, j = j0 + jl;
+      if (i >= n || j >= n || j <= i) continue;
+      const int64_t p = pair_index(i, j, n);
+      if (COVER) atomicAdd(reinterpret_cast<int32_t *>(out) + p, 1);
+      else reinterpret_cast<double *>(out)[p] = s_g[q] * rs[i] * rs[j];
+    }
+    __syncthreads();
+  }
+}
+
+// row checks (strictly increasing codes in [0, dim)), FP64 squared norms
+__global__ void sparse_rows_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                                   const float *__restrict__ val, int64_t n, int64_t dim,
+                                   double *__restrict__ rs, int32_t *bad) {
+  __shared__ double red[8];
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    double s = 0.0;
+    for (int64_t e = off[i] + threadIdx.x; e < off[i + 1]; e += blockDim.x) {
+      const int32_t k = idx[e];
+      if (k < 0 || k >= dim || (e > off[i] && idx[e - 1] >= k)) atomicExch(bad, 1);
+      s += (double)val[e] * (double)val[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      rs[i] = t > 0.0 ? 1.0 / sqrt(t) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    __syncthreads();
+  }
+}
+
+// cptr[c][i] = lower bound of c * W in row i's codes, relative to the row
+__global__ void sparse_cptr_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                                   int64_t n, int64_t n_chunks, int32_t *__restrict__ cptr) {
+  const int64_t total = (n_chunks + 1) * n;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = q / n, i = q - c * n;
+    const int64_t lo0 = off[i], hi0 = off[i + 1];
+    const int64_t key = c * (int64_t)W;
+    int64_t lo = lo0, hi = hi0;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)idx[mid] < key) lo = mid + 1;
+      else hi = mid;
+    }
+    cptr[q] = (int32_t)(lo - lo0);
+  }
+}
+
+}  // namespace
+
+void free_sparse(SparseStore &sp) {
+  dfree(sp.d_off);
+  dfree(sp.d_idx);
+  dfree(sp.d_val);
+  dfree(sp.d_cptr);
+  dfree(sp.d_rs);
+  dfree(sp.d_tiles);
+}
+
+ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
+  SparseStore &sp = it->sp;
+  const int64_t *off = d->offsets;
+  if (!off || off[0] != 0 || d->dim < 1 || d->dim > INT32_MAX) return AP_ERR_INVALID_ARG;
+  sp.n = d->n_items;
+  sp.dim = d->dim;
+  for (int64_t i = 0; i < sp.n; ++i) {
+    if (off[i + 1] < off[i]) return AP_ERR_INVALID_ARG;
+    if (off[i + 1] - off[i] > d->dim) return AP_ERR_INVALID_ARG;   // more entries than codes
+  }
+  sp.nnz = off[sp.n];
+  if (sp.nnz > 0 && (!d->indices || !d->data)) return AP_ERR_INVALID_ARG;
+  sp.n_chunks = (sp.dim + kSparseChunk - 1) / kSparseChunk;
+  AP_TRY(dmalloc(&sp.d_off, (size_t)sp.n + 1));
+  AP_TRY(dmalloc(&sp.d_idx, (size_t)std::max<int64_t>(sp.nnz, 1)));
+  AP_TRY(dmalloc(&sp.d_val, (size_t)std::max<int64_t>(sp.nnz, 1)));
+  AP_TRY(dmalloc(&sp.d_cptr, (size_t)(sp.n_chunks + 1) * std::max<int64_t>(sp.n, 1)));
+  AP_TRY(dmalloc(&sp.d_rs, (size_t)std::max<int64_t>(sp.n, 1)));
+  AP_TRY(cudaMemcpyAsync(sp.d_off, off, (size_t)(sp.n + 1) * 8, cudaMemcpyHostToDevice, s));
+  const cudaMemcpyKind kind = d->data_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (sp.nnz > 0) {
+    AP_TRY(cudaMemcpyAsync(sp.d_idx, d->indices, (size_t)sp.nnz * 4, kind, s));
+    AP_TRY(cudaMemcpyAsync(sp.d_val, d->data, (size_t)sp.nnz * 4, kind, s));
+  }
+  int32_t *d_bad = it->d_queue + 2;              // scratch word of the handle
+  AP_TRY(cudaMemsetAsync(d_bad, 0, 4, s));
+  if (sp.n > 0) {
+    const int g = (int)std::min<int64_t>(sp.n, 65535);
+    sparse_rows_kernel<<<g, 256, 0, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.n, sp.dim, sp.d_rs,
+                                         d_bad);
+    AP_TRY(cudaGetLastError());
+    const int64_t total = (sp.n_chunks + 1) * sp.n;
+    const int g2 = (int)std::min<int64_t>((total + 255) / 256, 65535);
+    sparse_cptr_kernel<<<g2, 256, 0, s>>>(sp.d_off, sp.d_idx, sp.n, sp.n_chunks, sp.d_cptr);
+    AP_TRY(cudaGetLastError());
+  }
+  std::vector<int32_t> tiles;
+  dc_block_pairs((sp.n + kSparseBlock - 1) / kSparseBlock, tiles);
+  sp.n_tiles = (int64_t)tiles.size() / 2;
+  AP_TRY(dmalloc(&sp.d_tiles, std::max<size_t>(tiles.size(), 2)));
+  if (!tiles.empty())
+    AP_TRY(cudaMemcpyAsync(sp.d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s));
+  int32_t bad = 0;
+  AP_TRY(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s));
+  AP_TRY(cudaStreamSynchronize(s));
+  if (bad) return AP_ERR_INVALID_ARG;
+  it->stats.tiles = sp.n_tiles;
+  it->stats.tile_m = it->stats.tile_n = kSparseBlock;
+  return AP_OK;
+}
+
+cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverage,
+                                 int32_t *queue, cudaStream_t s) {
+  if (sp.n_tiles <= 0) return cudaSuccess;
+  const size_t smem = (size_t)kWarps * W * 4 + (size_t)B * B * 8;
+  void (*kern)(const int64_t *, const int32_t *, const float *, const int32_t *, const double *,
+               int64_t, int64_t, const int32_t *, int64_t, int32_t *, void *) =
+      coverage ? sparse_cos_kernel<1> : sparse_cos_kernel<0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(num_sms(), sp.n_tiles);
+  kern<<<(int)grid, kThreads, smem, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.d_cptr, sp.d_rs, sp.n,
+                                         sp.n_chunks, sp.d_tiles, sp.n_tiles, queue, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ap

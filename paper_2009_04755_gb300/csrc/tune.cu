@@ -76,6 +76,12 @@ extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
   if (!it || !out) return AP_ERR_INVALID_ARG;
   out->k_split = 0;
   out->reserved = 0;
+  if (it->kind == AP_ITEMS_SPARSE) {
+    out->block_items = out->block_pts = kSparseBlock;
+    out->reg_r = out->sorted = 0;
+    out->rate = 0.0;
+    return AP_OK;
+  }
   if (it->kind == AP_ITEMS_VECTOR) {
     out->block_items = kTcTileM;
     out->block_pts = kTcTileN;
@@ -127,6 +133,7 @@ ap_status ap::set_vector_plan(ap_items *it, int32_t k_split) {
 
 extern "C" ap_status ap_set_plan(ap_items *it, const ap_plan *plan) {
   if (!it || !plan) return AP_ERR_INVALID_ARG;
+  if (it->kind == AP_ITEMS_SPARSE) return AP_ERR_UNSUPPORTED;
   if (it->kind == AP_ITEMS_VECTOR) {
     if (plan->block_items != kTcTileM || plan->block_pts != kTcTileN) return AP_ERR_INVALID_ARG;
     if (plan->k_split < -1 || plan->k_split > kMaxKSplit) return AP_ERR_INVALID_ARG;
@@ -145,7 +152,7 @@ extern "C" ap_status ap_set_plan(ap_items *it, const ap_plan *plan) {
 extern "C" ap_status ap_tune(ap_items *it, int32_t mode, void *stream, ap_plan *out) {
   if (!it) return AP_ERR_INVALID_ARG;
   if (mode != 0 && mode != 1) return AP_ERR_INVALID_ARG;
-  if (it->kind == AP_ITEMS_VECTOR) return AP_ERR_UNSUPPORTED;
+  if (it->kind == AP_ITEMS_VECTOR || it->kind == AP_ITEMS_SPARSE) return AP_ERR_UNSUPPORTED;
   if (mode == 1 && it->kind != AP_ITEMS_CLOUD2D) return AP_ERR_INVALID_ARG;
   CloudStore &c = it->cl;
   if (c.n < 2) {

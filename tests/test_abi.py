@@ -2,9 +2,12 @@
 function include/allpairs.h declares; host helpers agree with the oracle;
 argument validation fails cleanly before any device work.  No GPU needed."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -108,12 +111,36 @@ def test_invalid_args_rejected_before_device_work(ap):
     assert L.ap_get_stats(None, ctypes.byref(st)) == ap.AP_ERR_INVALID_ARG
 
 
-def test_desc_layout_matches_header(ap):
-    # offsets of the C struct on LP64: int32, int32, int64, 7 pointers, 2 int64,
-    # uint32 (+4 padding), uint64
-    assert ctypes.sizeof(ap.ItemsDesc) == 104
-    assert ap.ItemsDesc.slot_cache_bytes.offset == 96
-    assert ctypes.sizeof(ap.RunStats) == 56
+def test_struct_layouts_match_header(ap, tmp_path):
+    """The ctypes mirrors of the ABI structs against the header itself: a C
+    program compiled with include/allpairs.h prints sizeof and offsetof of
+    every field."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    structs = {"ap_items_desc": ap.ItemsDesc, "ap_run_stats": ap.RunStats, "ap_plan": ap.Plan}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "allpairs.h"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        cname, field, v = line.split()
+        got[(cname, field)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 @pytest.mark.parametrize("n,dim,slots", [(1000, 3000, 3), (4096, 65536, 6), (8192, 3 << 20, 16),
