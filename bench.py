@@ -421,6 +421,90 @@ def run_ooc_workload(args):
     return 0
 
 
+SPARSE_N, SPARSE_DIM = 2500, 20 ** 6
+# shared-memory / L1 data path of an SM: 128 bytes per clock; a probe of the
+# sparse cosine moves 12 (a 4-byte gather from the dense chunk + the 8-byte
+# entry it multiplies)
+L1_BYTES_PER_CLK_PER_SM = 128
+SPARSE_BYTES_PER_PROBE = 12
+
+
+def run_sparse_workload(args):
+    """Cosine of sparse composition vectors: 2500 items (Table I's
+    bioinformatics set) over 20^6 k-mer codes, 1e5-1.8e6 entries each."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2009_04755_gb300 as ap
+    torch.cuda.set_device(0)
+    n = args.n or SPARSE_N
+    off, idx, val = synth.sparse_cv(n, dim=SPARSE_DIM, seed=0, device="cuda", as_torch=True)
+    nnz = np.diff(off).astype(np.float64)
+    P = n * (n - 1) // 2
+    # the kernel streams row j's entries for every pair (i < j)
+    probes = float((nnz * np.arange(n)).sum())
+    items = ap.Items.from_sparse(off, idx, val, SPARSE_DIM)
+    out = torch.empty(P, dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        items.run_pairs(ap.AP_FN_COSINE, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        items.run_pairs(ap.AP_FN_COSINE, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    achieved = probes * SPARSE_BYTES_PER_PROBE / (ms / 1e3) / 1e9
+    peak = L1_BYTES_PER_CLK_PER_SM * 152 * sm_mhz * 1e6 / 1e9
+    line = {"metric": METRIC, "value": P / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-products/fp64-sums", "data": "synthetic",
+            "config": {"workload": f"cosine_sparse_n{n}", "n_items": n, "dim": SPARSE_DIM,
+                       "nnz_total": int(nnz.sum()), "pairs": P, "probes": probes},
+            "probes_per_s": probes / (ms / 1e3),
+            "roofline": {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "sparse_cos_kernel",
+                         "peak_kind": "128 B/clk/SM shared/L1 data path x 152 SMs x median SM "
+                                      "clock; 12 B per probe"},
+            "gpu_launches": args.steps}
+    if clk:
+        line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(7)
+        k = 200
+        rows = np.sort(rng.choice(n, size=2 * k, replace=False))
+        pi, pj = rows[0::2], rows[1::2]
+        # the sampled rows to the host, renumbered
+        sub = np.unique(np.concatenate([pi, pj]))
+        loc = {r: q for q, r in enumerate(sub)}
+        soff = np.zeros(len(sub) + 1, np.int64)
+        np.cumsum(nnz[sub].astype(np.int64), out=soff[1:])
+        sidx = torch.cat([idx[off[r]:off[r + 1]] for r in sub]).cpu().numpy()
+        sval = torch.cat([val[off[r]:off[r + 1]] for r in sub]).cpu().numpy()
+        li = np.array([loc[r] for r in pi]); lj = np.array([loc[r] for r in pj])
+        cores = os.cpu_count() or 1
+        oracle.build()
+        t0 = time.perf_counter()
+        ref = oracle.sparse_cosine(soff, sidx, sval, li, lj, n_threads=cores)
+        secs = time.perf_counter() - t0
+        p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+        got = out[p].cpu().numpy()
+        line["max_abs_err_sampled"] = float(np.abs(got - ref).max())
+        line["cpu_baseline"] = {"value": len(pi) / secs, "unit": "pairs/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{len(pi)} random pairs of the workload"}
+    items.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_cloud_workload(args):
     """Point-cloud workloads: overlap cost (2-D n=256, 3-D lognormal n=20000)
     and batched registration (2-D n=1024, 20 fused ascent steps per step)."""
@@ -572,7 +656,8 @@ def main():
     ap.add_argument("--workload", default="pearson_n8192_d1048576",
                     choices=["pearson_n8192_d1048576", "overlap2d_n256", "overlap3d_n20000",
                              "register2d_n1024", "pearson_ooc_n8192_d3145728",
-                             "particles2d_n256", "register_particles2d_n256"])
+                             "particles2d_n256", "register_particles2d_n256",
+                             "cosine_sparse_n2500"])
     ap.add_argument("--fn", default="overlap", choices=["overlap", "gmm_l2", "bhattacharyya"],
                     help="pair function of the cloud workloads")
     ap.add_argument("--ref-pairs", type=int, default=2000)
@@ -601,6 +686,8 @@ def main():
         return reference_arm(args)
     if args.workload == "pearson_ooc_n8192_d3145728":
         return run_ooc_workload(args)
+    if args.workload == "cosine_sparse_n2500":
+        return run_sparse_workload(args)
     if args.workload != "pearson_n8192_d1048576":
         return run_cloud_workload(args)
     return ours(args)

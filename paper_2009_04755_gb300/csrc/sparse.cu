@@ -8,15 +8,14 @@
 // space of `dim` codes (20^k k-mers), cut into chunks of kSparseChunk codes.
 // Schedule: persistent CTAs pop tiles (a block of 32 items I x a block of 32
 // items J, upper triangle in recursive quadrant order, Sec. IV-B) from an
-// atomic queue.  Each of the 16 warps owns one row i of I at a time and a
-// private dense array of one chunk in shared memory: per chunk it scatters
-// row i's entries into the array, then every lane walks its share of the
-// chunk's entries of each of the 32 rows j of J, gathering a_ik from the
-// array -- a dot product costs one shared-memory gather and one 8-byte entry
-// read per entry of row j, and row i's scatter is shared by the 32 rows j.
-// Per lane and row j the FP32 products are summed over up to 64 chunks and
-// then folded into FP64 (per pair, in shared memory); no CTA-wide barrier
-// runs inside the chunk loop.
+// atomic queue.  The 16 warps walk the chunks together, for half of I (16
+// rows) at a time: per chunk each warp scatters one row i into its dense
+// array of the chunk in shared memory, and after a barrier every lane reads
+// its share of the chunk's entries of the warp's two rows j (once, into
+// registers) and multiplies each against the 16 dense arrays -- a product
+// costs one shared-memory gather, the entry reads are shared by 16 rows i.
+// Per lane the FP32 products are summed over up to 64 chunks, then folded
+// into FP64 pair sums in shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -29,35 +28,27 @@ namespace ap {
 
 namespace {
 
-constexpr int kWarps = 16;
+constexpr int kWarps = 16;                   // rows i per pass (one dense array each)
 constexpr int kThreads = 32 * kWarps;
 constexpr int B = kSparseBlock;
+constexpr int kJ = B / kWarps;               // rows j per warp
+constexpr int kMinBlocks = 16 / kWarps;      // CTAs per SM the registers are sized for
 constexpr int W = kSparseChunk;
 constexpr int kFoldChunks = 64;
 
-// entries [lo, hi) of row `row` in chunk c, from the chunk-major pointers
-__device__ __forceinline__ void row_chunk(const int32_t *__restrict__ cptr, int64_t n,
-                                          const int64_t *__restrict__ off, int64_t row, int64_t c,
-                                          int64_t *lo, int64_t *hi) {
-  const int64_t base = off[row];
-  *lo = base + cptr[c * n + row];
-  *hi = base + cptr[(c + 1) * n + row];
-}
-
 template <int COVER>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
                   const float *__restrict__ val, const int32_t *__restrict__ cptr,
                   const double *__restrict__ rs, int64_t n, int64_t n_chunks,
                   const int32_t *__restrict__ tiles, int64_t n_tiles, int32_t *queue,
                   void *out) {
   extern __shared__ __align__(16) uint8_t smem[];
-  float *dense_all = reinterpret_cast<float *>(smem);                 // [kWarps][W]
-  double *s_g = reinterpret_cast<double *>(dense_all + kWarps * W);   // [B][B]
+  float *dense = reinterpret_cast<float *>(smem);                     // [kWarps][W]
+  double *s_g = reinterpret_cast<double *>(dense + kWarps * W);       // [B][B]
   __shared__ int s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float *dense = dense_all + warp * W;
-  for (int k = lane; k < W; k += 32) dense[k] = 0.f;
+  for (int k = threadIdx.x; k < kWarps * W; k += kThreads) dense[k] = 0.f;
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
@@ -71,58 +62,72 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     __syncthreads();
 
     if (!COVER) {
-      // the J block's row starts: lane l holds row j0 + l
-      const int64_t jrow = j0 + lane;
-      const bool jvalid = jrow < n;
-      const int64_t jbase = jvalid ? off[jrow] : 0;
-      for (int il = warp; il < B; il += kWarps) {
-        const int64_t i = i0 + il;
-        if (i >= n) break;
-        float acc[B];
+      // this warp's rows of J: jl = warp + h * kWarps
+      int64_t jrow[kJ], jbase[kJ];
 #pragma unroll
-        for (int jj = 0; jj < B; ++jj) acc[jj] = 0.f;
+      for (int h = 0; h < kJ; ++h) {
+        jrow[h] = j0 + warp + h * kWarps;
+        jbase[h] = jrow[h] < n ? off[jrow[h]] : 0;
+      }
+      for (int pass = 0; pass < B / kWarps; ++pass) {
+        // this warp scatters row i = i0 + pass * kWarps + warp into dense[warp]
+        const int64_t irow = i0 + pass * kWarps + warp;
+        const bool ivalid = irow < n;
+        const int64_t ibase = ivalid ? off[irow] : 0;
+        float *mine = dense + warp * W;
+        float acc[kJ][kWarps];
+#pragma unroll
+        for (int h = 0; h < kJ; ++h)
+#pragma unroll
+          for (int q = 0; q < kWarps; ++q) acc[h][q] = 0.f;
         int since = 0;
+        // chunk bounds, loaded one chunk ahead (the next chunk's pointer
+        // loads overlap this chunk's work)
+        int32_t ia = 0, ib = 0, ja[kJ], jb[kJ];
+        if (ivalid) ia = cptr[irow];
+#pragma unroll
+        for (int h = 0; h < kJ; ++h) ja[h] = jrow[h] < n ? cptr[jrow[h]] : 0;
         for (int64_t c = 0; c < n_chunks; ++c) {
-          int64_t a0, a1;
-          row_chunk(cptr, n, off, i, c, &a0, &a1);
-          if (a0 == a1) continue;                    // nothing of row i here
           const int32_t code0 = (int32_t)(c * W);
-          for (int64_t e = a0 + lane; e < a1; e += 32) dense[__ldg(idx + e) - code0] = __ldg(val + e);
-          // bounds of the 32 rows j in this chunk (one coalesced load each)
-          int32_t jlo = 0, jhi = 0;
-          if (jvalid) {
-            jlo = __ldg(cptr + c * n + jrow);
-            jhi = __ldg(cptr + (c + 1) * n + jrow);
-          }
-          __syncwarp();
+          if (ivalid) ib = cptr[(c + 1) * n + irow];
 #pragma unroll
-          for (int jj = 0; jj < B; ++jj) {
-            const int32_t lo = __shfl_sync(0xffffffffu, jlo, jj);
-            const int32_t hi = __shfl_sync(0xffffffffu, jhi, jj);
-            const int64_t jb = __shfl_sync(0xffffffffu, jbase, jj);
-            if (diag && jj <= il) continue;          // i < j only
-            for (int32_t e = lo + lane; e < hi; e += 32)
-              acc[jj] = fmaf(dense[__ldg(idx + jb + e) - code0], __ldg(val + jb + e), acc[jj]);
-          }
-          __syncwarp();
-          for (int64_t e = a0 + lane; e < a1; e += 32) dense[__ldg(idx + e) - code0] = 0.f;
-          __syncwarp();
-          if (++since == kFoldChunks) {
-            since = 0;
+          for (int h = 0; h < kJ; ++h) jb[h] = jrow[h] < n ? cptr[(c + 1) * n + jrow[h]] : 0;
+          const int64_t a0 = ibase + ia, a1 = ibase + ib;
+          for (int64_t e = a0 + lane; e < a1; e += 32) mine[__ldg(idx + e) - code0] = __ldg(val + e);
+          __syncthreads();
+          // every entry of the warp's rows j in this chunk against the
+          // kWarps rows i held in the dense arrays
 #pragma unroll
-            for (int jj = 0; jj < B; ++jj) {
-              double v = (double)acc[jj];
-              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-              if (lane == 0) s_g[il * B + jj] += v;
-              acc[jj] = 0.f;
+          for (int h = 0; h < kJ; ++h) {
+            // on the diagonal, rows j at or before every row i of this pass
+            // have no pair i < j here
+            if (jrow[h] >= n || (diag && warp + h * kWarps <= pass * kWarps)) continue;
+            const int64_t b0 = jbase[h] + ja[h], b1 = jbase[h] + jb[h];
+            for (int64_t e = b0 + lane; e < b1; e += 32) {
+              const int32_t k = __ldg(idx + e) - code0;
+              const float v = __ldg(val + e);
+#pragma unroll
+              for (int q = 0; q < kWarps; ++q) acc[h][q] = fmaf(dense[q * W + k], v, acc[h][q]);
             }
           }
-        }
+          __syncthreads();
+          for (int64_t e = a0 + lane; e < a1; e += 32) mine[__ldg(idx + e) - code0] = 0.f;
+          ia = ib;
 #pragma unroll
-        for (int jj = 0; jj < B; ++jj) {
-          double v = (double)acc[jj];
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) s_g[il * B + jj] += v;
+          for (int h = 0; h < kJ; ++h) ja[h] = jb[h];
+          if (++since == kFoldChunks || c + 1 == n_chunks) {
+            since = 0;
+            // fold the lanes' FP32 sums into the FP64 pair sums
+#pragma unroll
+            for (int h = 0; h < kJ; ++h)
+#pragma unroll
+              for (int q = 0; q < kWarps; ++q) {
+                double v = (double)acc[h][q];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) s_g[(pass * kWarps + q) * B + warp + h * kWarps] += v;
+                acc[h][q] = 0.f;
+              }
+          }
         }
       }
     }
@@ -255,7 +260,7 @@ cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverag
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(num_sms(), sp.n_tiles);
+  const int64_t grid = std::min<int64_t>((int64_t)num_sms() * kMinBlocks, sp.n_tiles);
   kern<<<(int)grid, kThreads, smem, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.d_cptr, sp.d_rs, sp.n,
                                          sp.n_chunks, sp.d_tiles, sp.n_tiles, queue, out);
   return cudaGetLastError();

@@ -128,7 +128,7 @@ def vectors_grouped(n: int, D: int, group: int = 16, shared_weight: float = 0.05
 
 def sparse_cv(n: int, dim: int = 20 ** 6, nnz=(100_000, 1_800_000), common: int = 4_000_000,
               common_boost: float = 8.0, shared_weight: float = 0.6, seed: int = 0,
-              device="cpu", sizes=None):
+              device="cpu", sizes=None, as_torch: bool = False):
     """Synthetic composition vectors (the bioinformatics workload's shape):
     sparse rows over a k-mer index space of ``dim`` codes (20^6 for k = 6),
     nnz_i ~ U[nnz[0], nnz[1]] (or ``sizes``), indices drawn per code with a
@@ -137,7 +137,8 @@ def sparse_cv(n: int, dim: int = 20 ** 6, nnz=(100_000, 1_800_000), common: int 
     g[code] + N(0, 1) with one global g ~ N(0, 1), so rows correlate on the
     codes they share.  Returns (offsets int64 [n+1], indices int32 [nnz]
     sorted per row, values float32 [nnz]) as numpy arrays; the draws run on
-    ``device`` with torch's seeded generator."""
+    ``device`` with torch's seeded generator (``as_torch``: indices and values
+    stay torch tensors on ``device``)."""
     import torch
 
     rng = _rng(seed + 15485863)
@@ -160,9 +161,16 @@ def sparse_cv(n: int, dim: int = 20 ** 6, nnz=(100_000, 1_800_000), common: int 
         thr[:common] = min(1.0, p * w_common)
         ids = torch.nonzero(u < thr).flatten()
         vals = shared_weight * g[ids] + torch.randn(len(ids), generator=gen, device=device)
-        idx_parts.append(ids.to(torch.int32).cpu().numpy())
-        val_parts.append(vals.float().cpu().numpy())
+        if as_torch:
+            idx_parts.append(ids.to(torch.int32))
+            val_parts.append(vals.float())
+        else:
+            idx_parts.append(ids.to(torch.int32).cpu().numpy())
+            val_parts.append(vals.float().cpu().numpy())
         off[i + 1] = off[i] + len(ids)
+    if as_torch:
+        return (off, torch.cat(idx_parts) if n else torch.zeros(0, dtype=torch.int32),
+                torch.cat(val_parts) if n else torch.zeros(0))
     return (off, np.concatenate(idx_parts) if n else np.zeros(0, np.int32),
             np.concatenate(val_parts) if n else np.zeros(0, np.float32))
 
