@@ -51,6 +51,43 @@ def dist_env():
     return ws, rank, local
 
 
+class Ranks:
+    """The multi-rank plumbing of a run: one process per GPU (torchrun), each
+    rank an independent replica of the workload (weak scaling, no collective
+    on the data path); the only collectives are the barrier around the timed
+    region and the max over ranks of its time."""
+
+    def __init__(self, backend: str = "nccl", device: str = "cuda"):
+        self.ws, self.rank, self.local = dist_env()
+        self.device = device
+        if self.ws > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        import torch
+        if self.ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        if self.device == "cuda":
+            torch.cuda.synchronize()
+
+    def max_over_ranks(self, v: float) -> float:
+        if self.ws == 1:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], device=self.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_rate(self, units_per_rank: float, steps: int, max_ms: float) -> float:
+        """Whole-job throughput: the units every rank processed over the
+        slowest rank's time."""
+        return units_per_rank * self.ws * steps / (max_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -169,23 +206,8 @@ def ours(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", "cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     n, D = args.n or N_ITEMS, args.dim or DIM
     P = n * (n - 1) // 2
@@ -223,7 +245,7 @@ def ours(args):
     ms = max_over_ranks(ms)
     gram_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
     gram_avg = sum(gram_ms) / len(gram_ms)
-    value = P * ws * args.steps / (ms / 1e3)
+    value = ranks.job_rate(P, args.steps, ms)
     if items.last_device_error() != 0:
         raise RuntimeError("device wait timed out during the benchmark")
 
