@@ -14,8 +14,11 @@
 // its share of the chunk's entries of the warp's two rows j (once, into
 // registers) and multiplies each against the 16 dense arrays -- a product
 // costs one shared-memory gather, the entry reads are shared by 16 rows i.
-// Per lane the FP32 products are summed over up to 64 chunks, then folded
-// into FP64 pair sums in shared memory.
+// Each warp copies the next chunk's entries of its rows (up to 64 per row)
+// into a two-stage shared-memory ring with cp.async while it works on the
+// current one, so the chunk loop does not wait on DRAM.  Per lane the FP32
+// products are summed over up to 64 chunks, then folded into FP64 pair sums
+// in shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,8 +36,31 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int B = kSparseBlock;
 constexpr int kJ = B / kWarps;               // rows j per warp
 constexpr int kMinBlocks = 16 / kWarps;      // CTAs per SM the registers are sized for
+constexpr int kStage = 64;                   // staged entries per row and chunk
 constexpr int W = kSparseChunk;
 constexpr int kFoldChunks = 64;
+
+// asynchronous 4-byte copy global -> shared; src_bytes 0 writes zeros and
+// reads nothing
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// One warp's staging of a chunk: up to kStage entries (2 per lane) of its row
+// i and of its kJ rows j, filled by cp.async one chunk ahead.
+struct WarpStage {
+  int32_t code[1 + kJ][kStage];
+  float val[1 + kJ][kStage];
+};
 
 template <int COVER>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
@@ -46,9 +72,11 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
   extern __shared__ __align__(16) uint8_t smem[];
   float *dense = reinterpret_cast<float *>(smem);                     // [kWarps][W]
   double *s_g = reinterpret_cast<double *>(dense + kWarps * W);       // [B][B]
+  WarpStage *stage = reinterpret_cast<WarpStage *>(s_g + B * B);      // [kWarps][2]
   __shared__ int s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < kWarps * W; k += kThreads) dense[k] = 0.f;
+  WarpStage *my_stage = stage + warp * 2;
 
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
@@ -62,18 +90,19 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     __syncthreads();
 
     if (!COVER) {
-      // this warp's rows of J: jl = warp + h * kWarps
-      int64_t jrow[kJ], jbase[kJ];
-#pragma unroll
-      for (int h = 0; h < kJ; ++h) {
-        jrow[h] = j0 + warp + h * kWarps;
-        jbase[h] = jrow[h] < n ? off[jrow[h]] : 0;
-      }
       for (int pass = 0; pass < B / kWarps; ++pass) {
-        // this warp scatters row i = i0 + pass * kWarps + warp into dense[warp]
-        const int64_t irow = i0 + pass * kWarps + warp;
-        const bool ivalid = irow < n;
-        const int64_t ibase = ivalid ? off[irow] : 0;
+        // the warp's rows: r = 0 its row i (scattered into dense[warp]),
+        // r = 1.. its rows j (jl = warp + (r - 1) * kWarps)
+        int64_t row[1 + kJ], base[1 + kJ];
+        bool valid[1 + kJ];
+        row[0] = i0 + pass * kWarps + warp;
+#pragma unroll
+        for (int h = 0; h < kJ; ++h) row[1 + h] = j0 + warp + h * kWarps;
+#pragma unroll
+        for (int r = 0; r <= kJ; ++r) {
+          valid[r] = row[r] < n;
+          base[r] = valid[r] ? off[row[r]] : 0;
+        }
         float *mine = dense + warp * W;
         float acc[kJ][kWarps];
 #pragma unroll
@@ -81,19 +110,50 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
 #pragma unroll
           for (int q = 0; q < kWarps; ++q) acc[h][q] = 0.f;
         int since = 0;
-        // chunk bounds, loaded one chunk ahead (the next chunk's pointer
-        // loads overlap this chunk's work)
-        int32_t ia = 0, ib = 0, ja[kJ], jb[kJ];
-        if (ivalid) ia = cptr[irow];
+        // chunk starts b0..b3 = cptr of chunks c .. c + 3 (relative to the row)
+        int32_t b0[1 + kJ], b1[1 + kJ], b2[1 + kJ], b3[1 + kJ];
+        auto bound = [&](int r, int64_t c) -> int32_t {
+          return (valid[r] && c <= n_chunks) ? cptr[c * n + row[r]] : 0;
+        };
+        // copies of chunk c's first kStage entries of every row into stage s
+        auto stage_copy = [&](int64_t c, const int32_t *lo, const int32_t *hi, int s) {
 #pragma unroll
-        for (int h = 0; h < kJ; ++h) ja[h] = jrow[h] < n ? cptr[jrow[h]] : 0;
+          for (int r = 0; r <= kJ; ++r) {
+#pragma unroll
+            for (int u = 0; u < kStage / 32; ++u) {
+              const int32_t e = lo[r] + u * 32 + lane;
+              const bool in = c < n_chunks && e < hi[r];
+              const int64_t g = in ? base[r] + e : 0;
+              cp_async4(&my_stage[s].code[r][u * 32 + lane], idx + g, in ? 4u : 0u);
+              cp_async4(&my_stage[s].val[r][u * 32 + lane], val + g, in ? 4u : 0u);
+            }
+          }
+          cp_async_commit();
+        };
+#pragma unroll
+        for (int r = 0; r <= kJ; ++r) {
+          b0[r] = bound(r, 0);
+          b1[r] = bound(r, 1);
+          b2[r] = bound(r, 2);
+        }
+        stage_copy(0, b0, b1, 0);
         for (int64_t c = 0; c < n_chunks; ++c) {
           const int32_t code0 = (int32_t)(c * W);
-          if (ivalid) ib = cptr[(c + 1) * n + irow];
+          const int s = (int)(c & 1);
 #pragma unroll
-          for (int h = 0; h < kJ; ++h) jb[h] = jrow[h] < n ? cptr[(c + 1) * n + jrow[h]] : 0;
-          const int64_t a0 = ibase + ia, a1 = ibase + ib;
-          for (int64_t e = a0 + lane; e < a1; e += 32) mine[__ldg(idx + e) - code0] = __ldg(val + e);
+          for (int r = 0; r <= kJ; ++r) b3[r] = bound(r, c + 3);
+          stage_copy(c + 1, b1, b2, s ^ 1);            // the next chunk, in flight
+          cp_async_wait_prev();                        // this chunk's copies landed
+          const WarpStage &st = my_stage[s];
+          // scatter row i (staged entries, then any beyond the stage)
+          const int32_t ni = b1[0] - b0[0];
+#pragma unroll
+          for (int u = 0; u < kStage / 32; ++u)
+            if (u * 32 + lane < ni) mine[st.code[0][u * 32 + lane] - code0] = st.val[0][u * 32 + lane];
+          for (int32_t e = kStage + lane; e < ni; e += 32) {
+            const int64_t g = base[0] + b0[0] + e;
+            mine[__ldg(idx + g) - code0] = __ldg(val + g);
+          }
           __syncthreads();
           // every entry of the warp's rows j in this chunk against the
           // kWarps rows i held in the dense arrays
@@ -101,20 +161,33 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
           for (int h = 0; h < kJ; ++h) {
             // on the diagonal, rows j at or before every row i of this pass
             // have no pair i < j here
-            if (jrow[h] >= n || (diag && warp + h * kWarps <= pass * kWarps)) continue;
-            const int64_t b0 = jbase[h] + ja[h], b1 = jbase[h] + jb[h];
-            for (int64_t e = b0 + lane; e < b1; e += 32) {
-              const int32_t k = __ldg(idx + e) - code0;
-              const float v = __ldg(val + e);
+            if (!valid[1 + h] || (diag && warp + h * kWarps <= pass * kWarps)) continue;
+            const int32_t nj = b1[1 + h] - b0[1 + h];
+#pragma unroll
+            for (int u = 0; u < kStage / 32; ++u) {
+              if (u * 32 + lane < nj) {
+                const int32_t k = st.code[1 + h][u * 32 + lane] - code0;
+                const float v = st.val[1 + h][u * 32 + lane];
+#pragma unroll
+                for (int q = 0; q < kWarps; ++q) acc[h][q] = fmaf(dense[q * W + k], v, acc[h][q]);
+              }
+            }
+            for (int32_t e = kStage + lane; e < nj; e += 32) {
+              const int64_t g = base[1 + h] + b0[1 + h] + e;
+              const int32_t k = __ldg(idx + g) - code0;
+              const float v = __ldg(val + g);
 #pragma unroll
               for (int q = 0; q < kWarps; ++q) acc[h][q] = fmaf(dense[q * W + k], v, acc[h][q]);
             }
           }
           __syncthreads();
-          for (int64_t e = a0 + lane; e < a1; e += 32) mine[__ldg(idx + e) - code0] = 0.f;
-          ia = ib;
 #pragma unroll
-          for (int h = 0; h < kJ; ++h) ja[h] = jb[h];
+          for (int u = 0; u < kStage / 32; ++u)
+            if (u * 32 + lane < ni) mine[st.code[0][u * 32 + lane] - code0] = 0.f;
+          for (int32_t e = kStage + lane; e < ni; e += 32)
+            mine[__ldg(idx + base[0] + b0[0] + e) - code0] = 0.f;
+#pragma unroll
+          for (int r = 0; r <= kJ; ++r) { b0[r] = b1[r]; b1[r] = b2[r]; b2[r] = b3[r]; }
           if (++since == kFoldChunks || c + 1 == n_chunks) {
             since = 0;
             // fold the lanes' FP32 sums into the FP64 pair sums
@@ -129,6 +202,7 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
               }
           }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");   // the last (empty) group
       }
     }
     __syncthreads();
@@ -252,7 +326,8 @@ ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
 cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverage,
                                  int32_t *queue, cudaStream_t s) {
   if (sp.n_tiles <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kWarps * W * 4 + (size_t)B * B * 8;
+  const size_t smem = (size_t)kWarps * W * 4 + (size_t)B * B * 8 +
+                      (size_t)kWarps * 2 * sizeof(WarpStage);
   void (*kern)(const int64_t *, const int32_t *, const float *, const int32_t *, const double *,
                int64_t, int64_t, const int32_t *, int64_t, int32_t *, void *) =
       coverage ? sparse_cos_kernel<1> : sparse_cos_kernel<0>;
