@@ -127,7 +127,28 @@ typedef struct ap_items_desc {
    * the values.  indices and data are host or device pointers (data_on_host);
    * dim is the size of the index space (20^k for k-mers of k amino acids). */
   const int32_t *indices;
+  /* Vectors given encoded (the parse stage of l, Sec. III stage 2): with
+   * blobs != NULL (and data == NULL, data_on_host = 1, slot_cache_bytes > 0,
+   * ld = 0), row i is the blob_bytes[i] bytes at host pointer blobs[i] in
+   * `codec`; blobs and blob_bytes are host arrays that must outlive the
+   * handle.  Host threads (parse_threads, 0 = one per core) decode 256-row
+   * macros into page-locked host slots, host_cache_bytes of them (the
+   * second-level cache of Sec. IV-A; 0 = two slots, i.e. decode on every
+   * device-cache miss), from which the device cache is filled. */
+  const uint8_t *const *blobs;
+  const uint64_t *blob_bytes;
+  int32_t codec;           /* ap_codec */
+  int32_t parse_threads;
+  uint64_t host_cache_bytes;
 } ap_items_desc;
+
+/* Encodings of vectors for ap_items_desc.blobs. */
+typedef enum {
+  AP_CODEC_NONE = 0,
+  /* lossless: the bits of x_k XOR those of x_(k-1) (x_(-1) = +0) as an
+   * unsigned LEB128 varint, 1-5 bytes a value */
+  AP_CODEC_XOR_VARINT = 1
+} ap_codec;
 
 /* Run statistics of the last ap_run_pairs on a handle. */
 typedef struct ap_run_stats {
@@ -139,6 +160,8 @@ typedef struct ap_run_stats {
   int32_t tile_m, tile_n;   /* tile shape used (items x items) */
   int32_t order;            /* 0 = recursive quadrant order, 1 = row panels */
   int32_t reserved;
+  int64_t parsed_rows;      /* rows decoded by the parse stage during the run */
+  double host_hit_rate;     /* second-level cache: requests served without decoding */
 } ap_run_stats;
 
 /* Tile plan of a point-cloud set: blocks of at most block_items items and
@@ -334,6 +357,17 @@ ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy);
 ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t slot_cache_bytes,
                               int32_t policy, int64_t *n_slots, int64_t *n_loads,
                               int64_t *n_steps);
+
+/* ap_encode_vector -- encode dim floats in `codec` (host memory).  out NULL:
+ * *len = an upper bound of the encoded size.  Errors: AP_ERR_INVALID_ARG
+ * (NULL arguments, unknown codec, cap too small). */
+ap_status ap_encode_vector(const float *x, int64_t dim, int32_t codec, uint8_t *out,
+                           uint64_t cap, uint64_t *len);
+
+/* ap_decode_vector -- the parse stage's decoder for one row (host memory).
+ * Errors: AP_ERR_INVALID_ARG (unknown codec, malformed or short input, or
+ * input left over after dim values). */
+ap_status ap_decode_vector(const uint8_t *in, uint64_t len, int32_t codec, int64_t dim, float *x);
 
 /* Failure-path switches for testing the bounded device waits. */
 typedef enum {

@@ -34,7 +34,9 @@ class ItemsDesc(ctypes.Structure):
                 ("sigma", ctypes.c_void_p), ("weight", ctypes.c_void_p),
                 ("data", ctypes.c_void_p), ("dim", ctypes.c_int64), ("ld", ctypes.c_int64),
                 ("precisions", ctypes.c_uint32), ("slot_cache_bytes", ctypes.c_uint64),
-                ("indices", ctypes.c_void_p)]
+                ("indices", ctypes.c_void_p), ("blobs", ctypes.c_void_p),
+                ("blob_bytes", ctypes.c_void_p), ("codec", ctypes.c_int32),
+                ("parse_threads", ctypes.c_int32), ("host_cache_bytes", ctypes.c_uint64)]
 
 
 class RunStats(ctypes.Structure):
@@ -42,7 +44,8 @@ class RunStats(ctypes.Structure):
                 ("reuse_R", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64),
                 ("slot_hit_rate", ctypes.c_double), ("tile_m", ctypes.c_int32),
                 ("tile_n", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("parsed_rows", ctypes.c_int64),
+                ("host_hit_rate", ctypes.c_double)]
 
 
 class Plan(ctypes.Structure):
@@ -69,6 +72,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         sig = {
+            "ap_encode_vector": (i32, [vp, i64, i32, vp, ctypes.c_uint64, vp]),
+            "ap_decode_vector": (i32, [vp, ctypes.c_uint64, i32, i64, vp]),
             "ap_create_items": (i32, [ctypes.POINTER(ItemsDesc), vp, ctypes.POINTER(vp)]),
             "ap_update_items": (i32, [vp, vp, i32, vp]),
             "ap_run_pairs": (i32, [vp, i32, i32, vp, vp, vp]),
@@ -134,6 +139,29 @@ def plan_tiles(n: int, block: int):
 
 
 AP_OOC_RESIDENT_STREAM, AP_OOC_DC_LRU, AP_OOC_K_SLICED = 0, 1, 2
+AP_CODEC_NONE, AP_CODEC_XOR_VARINT = 0, 1
+
+
+def encode_vector(x, codec: int = AP_CODEC_XOR_VARINT) -> bytes:
+    """Encode one row (float32) for the parse stage."""
+    import numpy as np
+    x = np.ascontiguousarray(x, np.float32)
+    cap = ctypes.c_uint64()
+    check(lib().ap_encode_vector(x.ctypes.data, x.size, codec, None, 0, ctypes.byref(cap)),
+          "ap_encode_vector")
+    buf = (ctypes.c_uint8 * max(cap.value, 1))()
+    n = ctypes.c_uint64()
+    check(lib().ap_encode_vector(x.ctypes.data, x.size, codec, buf, cap.value, ctypes.byref(n)),
+          "ap_encode_vector")
+    return bytes(buf[:n.value])
+
+
+def decode_vector(blob: bytes, dim: int, codec: int = AP_CODEC_XOR_VARINT):
+    import numpy as np
+    x = np.empty(dim, np.float32)
+    src = (ctypes.c_uint8 * max(len(blob), 1)).from_buffer_copy(blob or b"\0")
+    check(lib().ap_decode_vector(src, len(blob), codec, dim, x.ctypes.data), "ap_decode_vector")
+    return x
 
 
 def plan_out_of_core(n: int, dim: int, slot_cache_bytes: int, policy: int = 0) -> dict:
@@ -253,6 +281,37 @@ class Items:
         check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
               "ap_create_items")
         return cls(h, AP_ITEMS_SPARSE, n)
+
+    @classmethod
+    def from_encoded(cls, blobs, dim: int, slot_cache_bytes: int, host_cache_bytes: int = 0,
+                     parse_threads: int = 0, codec: int = AP_CODEC_XOR_VARINT,
+                     stream=None) -> "Items":
+        """Out-of-core vector set whose rows arrive encoded (a list of bytes,
+        one per row); the library parses them on host threads into a pinned
+        host cache of host_cache_bytes and streams them through an HBM slot
+        cache of slot_cache_bytes."""
+        n = len(blobs)
+        bufs = [(ctypes.c_uint8 * max(len(b), 1)).from_buffer_copy(b or b"\0") for b in blobs]
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[ctypes.addressof(b) for b in bufs])
+        lens = (ctypes.c_uint64 * max(n, 1))(*[len(b) for b in blobs])
+        d = ItemsDesc()
+        d.kind = AP_ITEMS_VECTOR
+        d.data_on_host = 1
+        d.n_items = n
+        d.dim = int(dim)
+        d.precisions = 1 << AP_PREC_SPLIT_BF16
+        d.slot_cache_bytes = int(slot_cache_bytes)
+        d.blobs = ctypes.addressof(ptrs)
+        d.blob_bytes = ctypes.addressof(lens)
+        d.codec = int(codec)
+        d.parse_threads = int(parse_threads)
+        d.host_cache_bytes = int(host_cache_bytes)
+        h = ctypes.c_void_p()
+        check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
+              "ap_create_items")
+        obj = cls(h, AP_ITEMS_VECTOR, n)
+        obj._keep += [bufs, ptrs, lens]      # the library reads them on every run
+        return obj
 
     def update(self, X, stream=None):
         check(lib().ap_update_items(self._h, _ptr(X), 0 if X.is_cuda else 1, _stream_ptr(stream)),

@@ -85,6 +85,39 @@ struct OocStep {
 // ---------------------------------------------------------------------------
 // dense-vector storage
 // ---------------------------------------------------------------------------
+constexpr int64_t kOocMacroItems = 256;   // items per device / host cache slot
+
+// the second-level (host) cache of decoded macros and its parse threads
+// (hostcache.cu)
+struct HostCacheRelease;
+struct HostCache {
+  struct Impl;
+  int64_t n = 0, dim = 0, n_slots = 0;
+  size_t slot_floats = 0;
+  const uint8_t *const *blobs = nullptr;
+  const uint64_t *blob_bytes = nullptr;
+  int32_t codec = 0;
+  float *pinned = nullptr;                 // [n_slots][256][dim]
+  Impl *impl = nullptr;
+  HostCacheRelease *release_args = nullptr;
+  // counters (under the lock)
+  int64_t hits = 0, misses = 0, parsed_rows = 0;
+  bool bad_input = false;
+  ~HostCache();
+  ap_status init(int64_t n_items, int64_t dim, const uint8_t *const *blobs,
+                 const uint64_t *bytes, int32_t codec, int64_t slots, int threads);
+  void announce(const std::vector<int64_t> &macros);   // the run's requests, in order
+  int acquire(int64_t macro);                           // a ready slot, held
+  void release(int slot);
+  const float *slot_ptr(int slot) const { return pinned + (size_t)slot * slot_floats; }
+  void *release_arg(int slot);
+  static void CUDART_CB release_cb(void *arg);          // cudaLaunchHostFunc target
+  void worker();
+  void pump();
+};
+int64_t xor_varint_encode(const float *x, int64_t dim, uint8_t *out, uint64_t cap);
+bool xor_varint_decode(const uint8_t *in, uint64_t len, int64_t dim, float *x);
+
 struct VecStore {
   int64_t n = 0, D = 0, ld = 0;
   int64_t Dp = 0;                   // padded row length (multiple of 64)
@@ -99,6 +132,7 @@ struct VecStore {
   // out-of-core mode: HBM slot cache of 256-item macros
   bool out_of_core = false;
   const float *h_src = nullptr;
+  HostCache *host = nullptr;        // encoded items: decoded macros in pinned host slots
   uint64_t slot_cache_bytes = 0;
   int64_t n_macros = 0, n_slots = 0, group = 0, ring = 0;
   __nv_bfloat16 *d_pool_hi = nullptr, *d_pool_lo = nullptr;   // slot pool, blocked layout

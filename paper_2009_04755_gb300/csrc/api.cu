@@ -43,6 +43,7 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 void free_items(ap_items *it) {
   if (!it) return;
+  cudaDeviceSynchronize();          // queued host functions may still use the host cache
   CloudStore &c = it->cl;
   dfree(c.d_pts); dfree(c.d_lw); dfree(c.d_poff); dfree(c.d_cnt); dfree(c.d_perm);
   dfree(c.d_bstart); dfree(c.d_tiles);
@@ -260,7 +261,13 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   v.D = d->dim;
   v.ld = d->ld ? d->ld : d->dim;
   if (v.D < 2 || v.ld < v.D) return AP_ERR_INVALID_ARG;
-  if (v.n > 0 && !d->data) return AP_ERR_INVALID_ARG;
+  if (d->blobs) {
+    // encoded items: decoded rows are dense, only the out-of-core path reads them
+    if (d->data || !d->data_on_host || !d->slot_cache_bytes || d->ld) return AP_ERR_INVALID_ARG;
+    if (d->codec != AP_CODEC_XOR_VARINT || !d->blob_bytes) return AP_ERR_INVALID_ARG;
+  } else if (v.n > 0 && !d->data) {
+    return AP_ERR_INVALID_ARG;
+  }
   if (v.n > INT32_MAX / 2) return AP_ERR_UNSUPPORTED;
   v.precisions = d->precisions ? d->precisions : (1u << AP_PREC_SPLIT_BF16);
   if (v.precisions & ~((1u << AP_PREC_FP32) | (1u << AP_PREC_SPLIT_BF16)))

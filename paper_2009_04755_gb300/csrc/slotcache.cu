@@ -111,6 +111,8 @@ static void free_slices(VecStore &v) {
 }
 
 void free_out_of_core(VecStore &v) {
+  delete v.host;
+  v.host = nullptr;
   free_pool(v);
   free_slices(v);
   free_raw_ring(v);
@@ -445,6 +447,13 @@ ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
   v.out_of_core = true;
   v.h_src = d->data;
   v.slot_cache_bytes = d->slot_cache_bytes;
+  if (d->blobs) {
+    v.host = new (std::nothrow) HostCache();
+    if (!v.host) return AP_ERR_OOM;
+    const uint64_t macro_bytes = (uint64_t)kMacro * v.D * 4;
+    AP_TRY_ST(v.host->init(v.n, v.D, d->blobs, d->blob_bytes, d->codec,
+                           (int64_t)(d->host_cache_bytes / macro_bytes), d->parse_threads));
+  }
   v.n_macros = (v.n + kMacro - 1) / kMacro;
   const uint64_t slot_bytes = (uint64_t)kMacro * v.Dp * 2 * sizeof(__nv_bfloat16);
   v.n_slots = (int64_t)std::min<uint64_t>(d->slot_cache_bytes / slot_bytes, (uint64_t)v.n_macros);
@@ -460,6 +469,17 @@ ap_status create_out_of_core(const ap_items_desc *d, ap_items *it) {
 ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s) {
   VecStore &v = it->vec;
   if (v.ooc_policy == AP_OOC_K_SLICED) return run_slices(it, out, coverage, s);
+  int64_t hits0 = 0, misses0 = 0, parsed0 = 0;
+  if (v.host && !coverage) {
+    // the macro loads in order: the parse threads decode ahead of the copies
+    std::vector<int64_t> plan;
+    for (const OocStep &st : v.steps)
+      for (const auto &ld : st.loads) plan.push_back(ld.first);
+    hits0 = v.host->hits;
+    misses0 = v.host->misses;
+    parsed0 = v.host->parsed_rows;
+    v.host->announce(plan);
+  }
   const int64_t P = v.n * (v.n - 1) / 2;
   if (!coverage) AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
   // copies must follow whatever the caller queued before this call
@@ -476,8 +496,18 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
         const int64_t r0 = m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
         float *raw = v.d_raw + (size_t)b * kMacro * v.ld;
         if (v.ring_used[b]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[b], 0));
-        AP_TRY(cudaMemcpyAsync(raw, v.h_src + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
-                               cudaMemcpyHostToDevice, it->copy_stream));
+        if (v.host) {
+          // from the host cache (decoding the macro first on a miss); the
+          // slot is released once the copy has run
+          const int hs = v.host->acquire(m);
+          AP_TRY(cudaMemcpyAsync(raw, v.host->slot_ptr(hs), (size_t)rows * v.ld * 4,
+                                 cudaMemcpyHostToDevice, it->copy_stream));
+          AP_TRY(cudaLaunchHostFunc(it->copy_stream, HostCache::release_cb,
+                                    v.host->release_arg(hs)));
+        } else {
+          AP_TRY(cudaMemcpyAsync(raw, v.h_src + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
+                                 cudaMemcpyHostToDevice, it->copy_stream));
+        }
         AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
         AP_TRY(cudaStreamWaitEvent(s, v.ev_raw_ready[b], 0));
         AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, s));
@@ -511,6 +541,15 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
   it->stats.h2d_bytes = h2d;
   it->stats.slot_hit_rate =
       v.ooc_uses > 0 ? 1.0 - (double)v.ooc_loads / (double)v.ooc_uses : 1.0;
+  it->stats.parsed_rows = 0;
+  it->stats.host_hit_rate = 0.0;
+  if (v.host && !coverage) {
+    // the counters of this run (every request is enqueued by now)
+    const int64_t h = v.host->hits - hits0, m = v.host->misses - misses0;
+    it->stats.parsed_rows = v.host->parsed_rows - parsed0;
+    it->stats.host_hit_rate = h + m > 0 ? (double)h / (double)(h + m) : 0.0;
+    if (v.host->bad_input) return AP_ERR_INVALID_ARG;
+  }
   return AP_OK;
 }
 
@@ -528,6 +567,7 @@ extern "C" ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy) 
   if (e != cudaSuccess) return from_cuda(e);
   const bool was_sliced = v.ooc_policy == AP_OOC_K_SLICED;
   const bool sliced = policy == AP_OOC_K_SLICED;
+  if (sliced && v.host) return AP_ERR_UNSUPPORTED;    // slices need raw column ranges
   if (sliced) {
     // validate before giving up the slot pool
     int64_t cols, count, ring;

@@ -204,3 +204,57 @@ def test_out_of_core_column_slices_reject_small_cache(ap):
             it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
         r = it.run_pairs().cpu().numpy()     # the macro schedule is untouched
     assert np.isfinite(r).all()
+
+
+def test_encoded_items_parse_stage_and_host_cache(ap, oracle_lib):
+    """Rows given encoded: parsed on host threads into the pinned host cache
+    (the second-level cache), streamed through the device cache.  Without a
+    host cache (two staging slots) device-cache reloads mostly decode again;
+    with one that holds the set, a second run decodes nothing.  Results equal
+    the pinned-array run."""
+    n, D = 1000, 3000
+    X = synth.vectors_grouped(n, D, seed=61)
+    Xn = X.numpy()
+    blobs = [ap.binding.encode_vector(Xn[i]) for i in range(n)]
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(Xn, pi, pj)
+    tol = pearson_tolerance(Xn, pi, pj, 1)
+    cache = 3 * _slot_bytes(D)                       # 3 device slots for 4 macros: R > 1
+    with ap.Items.from_vectors(X.pin_memory(), slot_cache_bytes=cache) as it:
+        base = it.run_pairs().cpu().numpy()
+        loads = it.stats()["item_loads"]
+    with ap.Items.from_encoded(blobs, D, slot_cache_bytes=cache, host_cache_bytes=0,
+                               parse_threads=4) as it:
+        got = it.run_pairs().cpu().numpy()
+        st = it.stats()
+        assert it.last_device_error() == 0
+    assert np.all(np.abs(got - ref) <= tol)
+    assert np.abs(got - base).max() <= 1e-12
+    # two host slots even without a cache: a reload may still find its macro
+    assert st["item_loads"] == loads and n <= st["parsed_rows"] <= loads
+    host = 4 * 256 * D * 4                           # every macro decoded fits
+    with ap.Items.from_encoded(blobs, D, slot_cache_bytes=cache, host_cache_bytes=host) as it:
+        first = it.run_pairs().cpu().numpy()
+        s1 = it.stats()
+        second = it.run_pairs().cpu().numpy()
+        s2 = it.stats()
+    assert np.abs(first - base).max() <= 1e-12 and np.abs(second - base).max() <= 1e-12
+    assert s1["parsed_rows"] == n and s2["parsed_rows"] == 0
+    assert s2["host_hit_rate"] == 1.0 and s1["host_hit_rate"] < 1.0
+
+
+def test_encoded_items_reject(ap):
+    n, D = 300, 256
+    X = synth.vectors_grouped(n, D, seed=62).numpy()
+    blobs = [ap.binding.encode_vector(X[i]) for i in range(n)]
+    cache = 3 * _slot_bytes(D)
+    with ap.Items.from_encoded(blobs, D, slot_cache_bytes=cache) as it:
+        with pytest.raises(ap.APError):              # slices need raw column ranges
+            it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+    bad = list(blobs)
+    bad[7] = bad[7][:-3]                             # a truncated row
+    with ap.Items.from_encoded(bad, D, slot_cache_bytes=cache) as it:
+        with pytest.raises(ap.APError):
+            it.run_pairs()
+    with pytest.raises(ap.APError):                  # encoded rows need the out-of-core path
+        ap.Items.from_encoded(blobs, D, slot_cache_bytes=0)
