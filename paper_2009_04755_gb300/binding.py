@@ -153,7 +153,7 @@ def encode_vector(x, codec: int = AP_CODEC_XOR_VARINT) -> bytes:
     n = ctypes.c_uint64()
     check(lib().ap_encode_vector(x.ctypes.data, x.size, codec, buf, cap.value, ctypes.byref(n)),
           "ap_encode_vector")
-    return bytes(buf[:n.value])
+    return ctypes.string_at(buf, n.value)
 
 
 def decode_vector(blob: bytes, dim: int, codec: int = AP_CODEC_XOR_VARINT):

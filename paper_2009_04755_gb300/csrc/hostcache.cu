@@ -74,13 +74,19 @@ struct HostCache::Impl {
     int pins = 0;
     bool reserved = false;  // pinned ahead of its request by the prefetcher
     bool reserved_hit = false;   // ... while it was already in the cache
+    int pending = 0;        // row jobs of the macro still decoding
     uint64_t last_use = 0;
   };
   std::mutex mu;
   std::condition_variable cv;
   std::vector<Slot> slots;
   std::unordered_map<int64_t, int> where;
-  std::deque<std::pair<int64_t, int>> jobs;
+  struct Job {
+    int64_t macro;
+    int slot;
+    int64_t r0, r1;        // rows of the macro
+  };
+  std::deque<Job> jobs;
   std::vector<int64_t> plan;      // announced requests, in order
   size_t plan_pos = 0;
   std::vector<std::thread> workers;
@@ -130,9 +136,12 @@ ap_status HostCache::init(int64_t n_items, int64_t dim_, const uint8_t *const *b
   return AP_OK;
 }
 
+// rows of a macro decoded per job, so that all threads share one macro
+constexpr int64_t kRowsPerJob = 8;
+
 void HostCache::worker() {
   for (;;) {
-    std::pair<int64_t, int> job;
+    Impl::Job job;
     {
       std::unique_lock<std::mutex> g(impl->mu);
       impl->cv.wait(g, [this] { return impl->stop || !impl->jobs.empty(); });
@@ -140,20 +149,34 @@ void HostCache::worker() {
       job = impl->jobs.front();
       impl->jobs.pop_front();
     }
-    const int64_t r0 = job.first * kOocMacroItems;
-    const int64_t rows = std::min<int64_t>(kOocMacroItems, n - r0);
-    float *dst = pinned + (size_t)job.second * slot_floats;
+    const int64_t g0 = job.macro * kOocMacroItems;
+    float *dst = pinned + (size_t)job.slot * slot_floats;
     bool ok = true;
-    for (int64_t r = 0; r < rows; ++r)
-      ok = ok && xor_varint_decode(blobs[r0 + r], blob_bytes[r0 + r], dim, dst + (size_t)r * dim);
+    for (int64_t r = job.r0; r < job.r1; ++r)
+      ok = ok && xor_varint_decode(blobs[g0 + r], blob_bytes[g0 + r], dim, dst + (size_t)r * dim);
+    bool done;
     {
       std::lock_guard<std::mutex> g(impl->mu);
-      impl->slots[job.second].state = 2;
-      parsed_rows += rows;
+      Impl::Slot &sl = impl->slots[job.slot];
+      done = --sl.pending == 0;
+      if (done) sl.state = 2;
+      parsed_rows += job.r1 - job.r0;
       if (!ok) bad_input = true;
     }
-    impl->cv.notify_all();
+    if (done) impl->cv.notify_all();
   }
+}
+
+// queue the row jobs of `macro` into slot s (caller holds the lock)
+static void queue_macro(HostCache::Impl *impl, int64_t n, int64_t macro, int s) {
+  const int64_t rows = std::min<int64_t>(kOocMacroItems, n - macro * kOocMacroItems);
+  int pending = 0;
+  for (int64_t r0 = 0; r0 < rows; r0 += kRowsPerJob) {
+    impl->jobs.push_back({macro, s, r0, std::min<int64_t>(rows, r0 + kRowsPerJob)});
+    ++pending;
+  }
+  impl->slots[s].pending = pending;
+  if (pending == 0) impl->slots[s].state = 2;
 }
 
 // a slot for `macro` (caller holds the lock): an empty one, else the least
@@ -197,7 +220,7 @@ void HostCache::pump() {
     sl.reserved_hit = false;
     sl.last_use = ++impl->clock;
     impl->where[m] = v;
-    impl->jobs.emplace_back(m, v);
+    queue_macro(impl, n, m, v);
     ++held;
     ++impl->plan_pos;
   }
@@ -248,7 +271,7 @@ int HostCache::acquire(int64_t macro) {
       sl.reserved = false;
       sl.last_use = ++impl->clock;
       impl->where[macro] = v;
-      impl->jobs.emplace_back(macro, v);
+      queue_macro(impl, n, macro, v);
       ++misses;
       impl->cv.notify_all();
       impl->cv.wait(g, [&] { return impl->slots[v].state == 2; });
