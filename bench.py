@@ -269,8 +269,10 @@ def ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (32 GiB raw + 32 GiB hi/lo) far larger than L2"},
             "roofline": roofline, "gram_ms": gram_avg,
-            # per step: vec_mean, vec_split, vec_finalize, gram_tc (+ the split-K scaling pass)
-            "gpu_launches": (5 if k_split else 4) * args.steps}
+            # per step: vec_shift, vec_split, slice_stats, vec_split over the rows
+            # centred again (normally none), slice_stats, gram_tc, and the pass
+            # that scales (split-K) or corrects (whole tiles) the pairs
+            "gpu_launches": 7 * args.steps}
     if clk:
         line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
 

@@ -122,7 +122,10 @@ struct VecStore {
   int64_t n = 0, D = 0, ld = 0;
   int64_t Dp = 0;                   // padded row length (multiple of 64)
   uint32_t precisions = 0;
-  double *d_mu = nullptr, *d_ss = nullptr, *d_rs = nullptr;   // FP64 per item
+  double *d_mu = nullptr, *d_ss = nullptr, *d_rs = nullptr;   // FP64 per item (d_mu: the shift)
+  double *d_delta_all = nullptr;    // mean - shift per item
+  double *d_partc = nullptr;        // [n][kSplitParts] partial sums of c
+  int32_t *d_recentre = nullptr;    // [n + 1]: count, rows centred again
   double *d_part = nullptr;         // [n][kSplitParts] partial sums of c^2
   int64_t n_rows_alloc = 0;         // rows rounded up to the row block
   __nv_bfloat16 *d_hi = nullptr, *d_lo = nullptr;              // [n][Dp]
@@ -255,7 +258,7 @@ void make_blocks(const std::vector<int64_t> &poff, const std::vector<int64_t> &c
 constexpr int kRowBlock = 128;
 constexpr int kTcKBlock = 32;     // bf16 columns per block (64 bytes per row)
 constexpr int kF32KBlock = 16;    // fp32 columns per block (64 bytes per row)
-constexpr int kSplitParts = 64;   // FP64 partials of sum c^2 per row
+constexpr int kSplitParts = 16;   // FP64 partials of sum c^2 and sum c per row
 __host__ __device__ __forceinline__ size_t blocked_offset(int64_t row, int64_t k, int64_t nkb,
                                                           int kblk) {
   return ((size_t)(row / kRowBlock) * nkb + (size_t)(k / kblk)) * ((size_t)kRowBlock * kblk) +
@@ -263,10 +266,23 @@ __host__ __device__ __forceinline__ size_t blocked_offset(int64_t row, int64_t k
 }
 cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, double *mu,
                             cudaStream_t s);
-// rows [row0, row0 + n) of the item set, X pointing at row row0
-cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D, int64_t ld,
-                             int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                             float *c32, double *part, double *ss, double *rs, cudaStream_t s);
+// the single-pass load pipeline of vectors: per row a shift (the mean of
+// evenly spread samples), then the centred split / FP32 copies and the FP64
+// sums of c and c^2 in one pass, then delta = mean - shift, ss and rs; rows
+// whose shift missed the mean by D delta^2 > ss / 64 are redone from the
+// exact mean.  recentre: device int32 [n + 1] scratch (count, rows).
+cudaError_t launch_vec_prep(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D,
+                            int64_t ld, int64_t Dp, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                            float *c32, double *shift, double *part, double *part_c,
+                            double *delta, double *ss, double *rs, int32_t *recentre,
+                            cudaStream_t s);
+// out[p] -= (D delta_i rs_i)(delta_j rs_j) over the packed triangle: the
+// mean correction of pairs the Gram kernel already scaled by rs_i rs_j
+cudaError_t launch_pair_correct(double *out, const double *rs, const double *delta, int64_t n,
+                                int64_t D, cudaStream_t s);
+// out[p] = (out[p] - D delta_i delta_j) rs_i rs_j over the packed triangle
+cudaError_t launch_pair_finalize(double *out, const double *rs, const double *delta, int64_t n,
+                                 int64_t D, cudaStream_t s);
 // one column chunk [.., cols) of rows row0.., centred on per-row shifts (the
 // rows' blocked copies hold cols_p >= cols columns); FP64 partials of
 // sum c^2 and sum c are set (first_chunk) or accumulated per row
@@ -282,7 +298,8 @@ cudaError_t launch_slice_finalize(const double *part, const double *part_c, int6
 cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
                             const int32_t *tiles, int64_t n_tiles, int32_t *queue,
                             void *out, int coverage, int64_t row0, int64_t n_total,
-                            cudaStream_t s);
+                            cudaStream_t s, const double *delta = nullptr,
+                            int64_t D = 0);
 // tensor-core split-BF16 Gram (gram_tc.cu)
 constexpr int kTcTileM = 128;    // rows of the I block per tile
 constexpr int kTcTileN = 256;    // rows of the J block per tile
@@ -313,9 +330,6 @@ void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t gro
 // ranges per tile (0 whole tiles, -1 the default rule of default_k_split)
 int32_t default_k_split(int64_t n_tiles, int64_t Dp);
 ap_status set_vector_plan(ap_items *it, int32_t k_split);
-// out[p] *= rs_i rs_j over the packed upper triangle (split-K partial sums
-// are added into out first)
-cudaError_t launch_gram_finalize(double *out, const double *rs, int64_t n, cudaStream_t s);
 
 // clouds (overlap.cu)
 cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,

@@ -51,6 +51,7 @@ void free_items(ap_items *it) {
   dfree(c.d_self);
   VecStore &v = it->vec;
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
+  dfree(v.d_partc); dfree(v.d_delta_all); dfree(v.d_recentre);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
   dfree(v.d_panel_units);
   free_out_of_core(v);
@@ -210,10 +211,9 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
   const bool split = (v.precisions & (1u << AP_PREC_SPLIT_BF16)) != 0;
   const bool f32 = (v.precisions & (1u << AP_PREC_FP32)) != 0;
   if (!on_host) {
-    AP_TRY(launch_vec_mean(data, v.n, v.D, v.ld, v.d_mu, s));
-    AP_TRY(launch_vec_split(data, 0, 0, v.n, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
-                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
-                            v.d_rs, s));
+    AP_TRY(launch_vec_prep(data, 0, 0, v.n, v.D, v.ld, v.Dp, split ? v.d_hi : nullptr,
+                           split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_mu, v.d_part,
+                           v.d_partc, v.d_delta_all, v.d_ss, v.d_rs, v.d_recentre, s));
     return AP_OK;
   }
   // host source: two staging buffers, copies on the copy stream overlap the
@@ -239,11 +239,10 @@ ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s)
                           it->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(copied[b], it->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[b], 0);
-    if (e == cudaSuccess) e = launch_vec_mean(stage, nr, v.D, v.ld, v.d_mu + r0, s);
     if (e == cudaSuccess)
-      e = launch_vec_split(stage, r0, r0, nr, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
-                           split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
-                           v.d_rs, s);
+      e = launch_vec_prep(stage, r0, r0, nr, v.D, v.ld, v.Dp, split ? v.d_hi : nullptr,
+                          split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_mu, v.d_part,
+                          v.d_partc, v.d_delta_all, v.d_ss, v.d_rs, v.d_recentre, s);
     if (e == cudaSuccess) e = cudaEventRecord(done[b], s);
   }
   if (e != cudaSuccess) st = from_cuda(e);
@@ -278,6 +277,9 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   AP_TRY(dmalloc(&v.d_ss, nn));
   AP_TRY(dmalloc(&v.d_rs, nn));
   AP_TRY(dmalloc(&v.d_part, (size_t)nn * kSplitParts));
+  AP_TRY(dmalloc(&v.d_partc, (size_t)nn * kSplitParts));
+  AP_TRY(dmalloc(&v.d_delta_all, nn));
+  AP_TRY(dmalloc(&v.d_recentre, nn + 1));
   // out-of-core: items stay in host memory and stream through the slot cache
   if (d->slot_cache_bytes) return create_out_of_core(d, it);
   // blocked copies cover whole row blocks; the padding rows stay zero
@@ -457,7 +459,8 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_panel_units,
                             v.n_panel_units, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
                             it->wait_budget_ns, it->debug, s));
-      AP_TRY(launch_gram_finalize(reinterpret_cast<double *>(out), v.d_rs, v.n, s));
+      AP_TRY(launch_pair_finalize(reinterpret_cast<double *>(out), v.d_rs, v.d_delta_all, v.n,
+                                  v.D, s));
       it->stats.tiles = v.n_panel_units;
       it->stats.tile_m = kTcTileM;
       it->stats.tile_n = kTcTileN;
@@ -465,12 +468,15 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_tiles_tc, v.n_tiles_tc,
                             it->d_queue, it->d_status, v.d_g64, out, cover, 0,
                             it->wait_budget_ns, it->debug, s));
+      if (!cover)
+        AP_TRY(launch_pair_correct(reinterpret_cast<double *>(out), v.d_rs, v.d_delta_all, v.n,
+                                   v.D, s));
       it->stats.tiles = v.n_tiles_tc;
       it->stats.tile_m = kTcTileM;
       it->stats.tile_n = kTcTileN;
     } else {
       AP_TRY(launch_gram_f32(v.d_c32, v.n, v.Dp, v.d_rs, v.d_tiles_f32, v.n_tiles_f32,
-                             it->d_queue, out, cover, 0, v.n, s));
+                             it->d_queue, out, cover, 0, v.n, s, v.d_delta_all, v.D));
       it->stats.tiles = v.n_tiles_f32;
       it->stats.tile_m = 128;
       it->stats.tile_n = 128;

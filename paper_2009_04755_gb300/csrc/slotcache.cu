@@ -37,24 +37,8 @@ namespace {
 
 constexpr int64_t kMacro = 2 * kRowBlock;   // items per slot
 
-__global__ void ooc_finalize_kernel(double *__restrict__ out, const double *__restrict__ rs,
-                                    int64_t n) {
-  for (int64_t i = blockIdx.x; i < n - 1; i += gridDim.x) {
-    const double ri = rs[i];
-    const int64_t p0 = pair_index(i, i + 1, n);
-    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x)
-      out[p0 + (j - i - 1)] *= ri * rs[j];
-  }
-}
-
 }  // namespace
 
-cudaError_t launch_gram_finalize(double *out, const double *rs, int64_t n, cudaStream_t s) {
-  if (n < 2) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>(n - 1, 65535);
-  ooc_finalize_kernel<<<grid, 256, 0, s>>>(out, rs, n);
-  return cudaGetLastError();
-}
 
 static void free_raw_ring(VecStore &v) {
   dfree(v.d_raw);
@@ -510,10 +494,10 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
         }
         AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
         AP_TRY(cudaStreamWaitEvent(s, v.ev_raw_ready[b], 0));
-        AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, s));
         const size_t slot_off = (size_t)slot * kMacro * v.Dp;
-        AP_TRY(launch_vec_split(raw, r0, 0, rows, v.D, v.ld, v.Dp, v.d_mu, v.d_pool_hi + slot_off,
-                                v.d_pool_lo + slot_off, nullptr, v.d_part, v.d_ss, v.d_rs, s));
+        AP_TRY(launch_vec_prep(raw, r0, 0, rows, v.D, v.ld, v.Dp, v.d_pool_hi + slot_off,
+                               v.d_pool_lo + slot_off, nullptr, v.d_mu, v.d_part, v.d_partc,
+                               v.d_delta_all, v.d_ss, v.d_rs, v.d_recentre, s));
         AP_TRY(cudaEventRecord(v.ev_raw_free[b], s));
         v.ring_used[b] = 1;
         h2d += (uint64_t)rows * v.ld * 4;
@@ -527,11 +511,9 @@ ap_status run_out_of_core(ap_items *it, void *out, int coverage, cudaStream_t s)
                           it->d_queue, it->d_status, v.d_g64, out, coverage, 1,
                           it->wait_budget_ns, it->debug, s));
   }
-  if (!coverage && v.n > 1) {
-    const int grid = (int)std::min<int64_t>(v.n - 1, 65535);
-    ooc_finalize_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<double *>(out), v.d_rs, v.n);
-    AP_TRY(cudaGetLastError());
-  }
+  if (!coverage)
+    AP_TRY(launch_pair_finalize(reinterpret_cast<double *>(out), v.d_rs, v.d_delta_all, v.n, v.D,
+                                s));
   it->stats.tiles = 0;
   for (const OocStep &st : v.steps) it->stats.tiles += coverage ? st.n_cover : st.n_units;
   it->stats.tile_m = kTcTileM;
@@ -714,10 +696,10 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
                            cudaMemcpyHostToDevice, it->copy_stream));
     AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
     AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[b], 0));
-    AP_TRY(launch_vec_mean(raw, rows, v.D, v.ld, v.d_mu + r0, it->prep_stream));
-    AP_TRY(launch_vec_split(raw, r0, r0, rows, v.D, v.ld, v.Dp, v.d_mu, split ? v.d_hi : nullptr,
-                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_part, v.d_ss,
-                            v.d_rs, it->prep_stream));
+    AP_TRY(launch_vec_prep(raw, r0, r0, rows, v.D, v.ld, v.Dp, split ? v.d_hi : nullptr,
+                           split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_mu, v.d_part,
+                           v.d_partc, v.d_delta_all, v.d_ss, v.d_rs, v.d_recentre,
+                           it->prep_stream));
     AP_TRY(cudaEventRecord(v.ev_raw_free[b], it->prep_stream));
     AP_TRY(cudaEventRecord(v.ev_prepped[b], it->prep_stream));
     v.ring_used[b] = 1;
@@ -727,11 +709,7 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
                           v.stream_cols[m].second, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
                           it->wait_budget_ns, it->debug, s));
   }
-  if (v.n > 1) {
-    const int grid = (int)std::min<int64_t>(v.n - 1, 65535);
-    ooc_finalize_kernel<<<grid, 256, 0, s>>>(out, v.d_rs, v.n);
-    AP_TRY(cudaGetLastError());
-  }
+  AP_TRY(launch_pair_finalize(out, v.d_rs, v.d_delta_all, v.n, v.D, s));
   it->stats.item_loads = v.n;
   it->stats.reuse_R = 1.0;
   it->stats.h2d_bytes = (uint64_t)v.n * v.ld * 4;

@@ -2,18 +2,24 @@
 // (Sec. III, stage 4 of l) and the plain FP32 Gram path of the Pearson
 // correlation (the normalised cross correlation of Sec. V-A).
 //
-//   mu_i = (1/D) sum_k x_ik,  ss_i = sum_k (x_ik - mu_i)^2       (FP64 result)
-//   c_ik = x_ik - mu_i,  hi = bf16_rn(c),  lo = bf16_rn(c - hi)   (split-BF16)
-//   r_ij = sum_k c_ik c_jk / sqrt(ss_i ss_j)                       (FP64 scaling)
+//   s_i: a shift close to the mean (the mean of 1024 strided samples)
+//   c_ik = x_ik - s_i,  hi = bf16_rn(c),  lo = bf16_rn(c - hi)    (split-BF16)
+//   delta_i = (1/D) sum_k c_ik = mu_i - s_i,
+//   ss_i = sum_k c_ik^2 - delta_i sum_k c_ik = sum_k (x_ik - mu_i)^2 (FP64)
+//   r_ij = (sum_k c_ik c_jk - D delta_i delta_j) / sqrt(ss_i ss_j)  (FP64)
 //
+// One read of the rows does it all; rows whose shift missed the mean by
+// D delta^2 > ss / 64 are written again centred on the exact mean.
 // GB300 executes FP64 at a small fraction of its FP32 rate, so the
 // per-element work stays in FP32: short FP32 partial sums (64 elements per
 // thread) are folded into FP64 accumulators, and the centring subtracts the
-// FP64 mean as a two-float pair (x - mu_hi) - mu_lo, which keeps c accurate
-// to a few ulps of c itself even when |mu| >> |c|.
+// FP64 shift as a two-float pair (x - s_hi) - s_lo, which keeps c accurate
+// to a few ulps of c itself even when |s| >> |c|.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "ap_internal.h"
 
@@ -41,8 +47,9 @@ __device__ __forceinline__ double block_sum_f64(double v, double *red) {
   return r;
 }
 
-// Pass 1 of the load pipeline: one CTA per row, FP64 mean (FP32 partial sums
-// of 64 elements per thread folded into FP64).
+// The FP64 mean of each row's columns (the shift of column slices, taken
+// from their first chunk): one CTA per row, FP32 partial sums of 64 elements
+// per thread folded into FP64.
 template <bool VEC4>
 __global__ void __launch_bounds__(kStatsThreads)
 vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
@@ -82,125 +89,174 @@ vec_mean_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
   }
 }
 
-// Pass 2: centre each row against its FP64 mean (as the two-float pair
-// mu_hi + mu_lo), write the blocked split-BF16 and/or FP32 copies (zero
-// padded to Dp columns) and this CTA's FP64 partial of sum_k c_k^2.
-// Grid: x = kSplitParts column ranges of a row, y = rows (strided).
-// SLICE: one column chunk of the rows, centred on a per-row shift instead of
-// the mean; the CTA's partials of sum c^2 and sum c are added to `part` and
-// `part_c` (set when first_chunk) so they accumulate over the chunks.
-template <bool VEC4, bool SLICE>
-__global__ void __launch_bounds__(kSplitThreads)
+// Centre each row on its shift s (the two-float pair s_hi + s_lo), write the
+// blocked split-BF16 and/or FP32 copies (zero padded to Dp columns) and this
+// CTA's FP64 partials of sum_k c_k^2 and sum_k c_k into slot blockIdx.x of
+// the row (set when first_chunk, else added, so column chunks accumulate).
+// Grid: x = column ranges of a row (thread t of CTA b takes the float4
+// groups b * blockDim + t + m * stride), y = rows (strided), or only the rows
+// of list = [count, rows...].
+//
+// Blocked offsets advance by constants: the group stride is a multiple of 8
+// float4 (one 32-column block), so a thread's column within a block is fixed
+// and its block index grows by stride / 8 per step.
+__device__ __forceinline__ void split_store(const float c[4], __nv_bfloat16 *hi,
+                                            __nv_bfloat16 *lo, float *c32, size_t o_tc,
+                                            size_t o_32) {
+  if (hi) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(c[0], c[1]);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(c[2], c[3]);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    // c - hi is exact in FP32; its rounding to BF16 is the low part
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(c[0] - f01.x, c[1] - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(c[2] - f23.x, c[3] - f23.y);
+    uint2 hv, lv;
+    hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+    hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+    lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+    lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+    *reinterpret_cast<uint2 *>(hi + o_tc) = hv;
+    *reinterpret_cast<uint2 *>(lo + o_tc) = lv;
+  }
+  if (c32) *reinterpret_cast<float4 *>(c32 + o_32) = make_float4(c[0], c[1], c[2], c[3]);
+}
+
+template <bool VEC4>
+__global__ void __launch_bounds__(kSplitThreads, 4)
 vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, int64_t n,
                  int64_t D, int64_t ld, int64_t Dp, const double *__restrict__ mu,
                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
                  float *__restrict__ c32, double *__restrict__ part,
-                 double *__restrict__ part_c, int first_chunk) {
-  __shared__ double red[33];
+                 double *__restrict__ part_c, int first_chunk,
+                 const int32_t *__restrict__ list) {
+  __shared__ double2 red[kSplitThreads];
   const int64_t q4 = Dp >> 2;                  // float4 groups per padded row
+  const int64_t qf = VEC4 ? (D >> 2) : 0;      // groups wholly inside the row
   const int64_t nkb_tc = Dp / kTcKBlock, nkb_32 = Dp / kF32KBlock;
-  for (int64_t lr = blockIdx.y; lr < n; lr += gridDim.y) {
+  const int64_t stq = (int64_t)gridDim.x * blockDim.x;
+  const int64_t qa = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr size_t kTileTc = (size_t)kRowBlock * kTcKBlock, kTile32 = (size_t)kRowBlock * kF32KBlock;
+  const size_t d_tc = (size_t)(stq >> 3) * kTileTc, d_32 = (size_t)(stq >> 2) * kTile32;
+  const int64_t nrows = list ? (int64_t)list[0] : n;
+  for (int64_t t = blockIdx.y; t < nrows; t += gridDim.y) {
+    const int64_t lr = list ? (int64_t)list[1 + t] : t;
     const int64_t row = row0 + lr;             // global item index (statistics)
     const int64_t orow = out_row0 + lr;        // row of the blocked copies
     const float *x = X + lr * ld;
     const double m = mu[row];
     const float mh = (float)m;
     const float ml = (float)(m - (double)mh);
+    const int64_t rb = orow / kRowBlock, ri = orow % kRowBlock;
+    size_t o_tc = ((size_t)rb * nkb_tc + (size_t)(qa >> 3)) * kTileTc + (size_t)ri * kTcKBlock +
+                  4 * (size_t)(qa & 7);
+    size_t o_32 = ((size_t)rb * nkb_32 + (size_t)(qa >> 2)) * kTile32 + (size_t)ri * kF32KBlock +
+                  4 * (size_t)(qa & 3);
     double acc = 0.0, acc_c = 0.0;
     float psum = 0.f, psum_c = 0.f;
-    const int64_t stq = (int64_t)gridDim.x * blockDim.x;
-    int iter = 0;
-    // two float4 groups per trip, both loads issued before either is used
-    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q0 < q4; q0 += 2 * stq) {
-      float vv[2][4];
+    int64_t q = qa;
+    // four groups per trip, all loads issued before any is used
+    for (int trips = 0; q + 3 * stq < qf; q += 4 * stq) {
+      float4 v[4];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int64_t k = (q0 + u * stq) << 2;
-        if (VEC4 && k + 3 < D) {
-          const float4 t = __ldg(reinterpret_cast<const float4 *>(x + k));
-          vv[u][0] = t.x; vv[u][1] = t.y; vv[u][2] = t.z; vv[u][3] = t.w;
-        } else {
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4 *>(x) + q + u * stq);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) vv[u][e] = (k + e < D) ? __ldg(x + k + e) : 0.f;
-        }
+      for (int u = 0; u < 4; ++u) {
+        const float c[4] = {(v[u].x - mh) - ml, (v[u].y - mh) - ml, (v[u].z - mh) - ml,
+                            (v[u].w - mh) - ml};
+        psum += (c[0] * c[0] + c[1] * c[1]) + (c[2] * c[2] + c[3] * c[3]);
+        psum_c += (c[0] + c[1]) + (c[2] + c[3]);
+        split_store(c, hi, lo, c32, o_tc, o_32);
+        o_tc += d_tc;
+        o_32 += d_32;
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-      const int64_t q = q0 + u * stq;
-      if (q >= q4) break;
-      const int64_t k = q << 2;
-      const float *v = vv[u];
-      float c[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) c[e] = (k + e < D) ? (v[e] - mh) - ml : 0.f;
-      psum += (c[0] * c[0] + c[1] * c[1]) + (c[2] * c[2] + c[3] * c[3]);
-      if (SLICE) psum_c += (c[0] + c[1]) + (c[2] + c[3]);
-      if (hi) {
-        __nv_bfloat16 h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          h[e] = __float2bfloat16_rn(c[e]);
-          l[e] = __float2bfloat16_rn(c[e] - __bfloat162float(h[e]));   // c - hi is exact
-        }
-        uint2 hv, lv;
-        hv.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-        hv.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
-        lv.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
-        lv.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
-        const size_t o = blocked_offset(orow, k, nkb_tc, kTcKBlock);
-        *reinterpret_cast<uint2 *>(hi + o) = hv;
-        *reinterpret_cast<uint2 *>(lo + o) = lv;
-      }
-      if (c32) {
-        const size_t o = blocked_offset(orow, k, nkb_32, kF32KBlock);
-        *reinterpret_cast<float4 *>(c32 + o) = make_float4(c[0], c[1], c[2], c[3]);
-      }
-      }
-      // fold every 16 float4 (64 elements) into FP64
-      if ((++iter & 7) == 0) {
+      if (++trips == 4) {                      // 64 elements per FP32 partial
         acc += (double)psum;
-        psum = 0.f;
-        if (SLICE) { acc_c += (double)psum_c; psum_c = 0.f; }
+        acc_c += (double)psum_c;
+        psum = psum_c = 0.f;
+        trips = 0;
       }
+    }
+    // the rest one group at a time, bounds checked (ragged end, padding)
+    for (; q < q4; q += stq) {
+      const int64_t k = q << 2;
+      float c[4];
+      if (VEC4 && k + 3 < D) {
+        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(x + k));
+        c[0] = (t4.x - mh) - ml; c[1] = (t4.y - mh) - ml;
+        c[2] = (t4.z - mh) - ml; c[3] = (t4.w - mh) - ml;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[e] = (k + e < D) ? (__ldg(x + k + e) - mh) - ml : 0.f;
+      }
+      psum += (c[0] * c[0] + c[1] * c[1]) + (c[2] * c[2] + c[3] * c[3]);
+      psum_c += (c[0] + c[1]) + (c[2] + c[3]);
+      split_store(c, hi, lo, c32, o_tc, o_32);
+      o_tc += d_tc;
+      o_32 += d_32;
     }
     acc += (double)psum;
-    const double s = block_sum_f64(acc, red);
-    const size_t slot = (size_t)row * gridDim.x + blockIdx.x;
-    if (SLICE) {
-      acc_c += (double)psum_c;
-      const double sc = block_sum_f64(acc_c, red);
-      if (threadIdx.x == 0) {
-        part[slot] = first_chunk ? s : part[slot] + s;
-        part_c[slot] = first_chunk ? sc : part_c[slot] + sc;
+    acc_c += (double)psum_c;
+    // FP64 runs at a small fraction of the FP32 rate: one warp adds the
+    // CTA's partials from shared memory instead of a shuffle tree per warp
+    red[threadIdx.x] = make_double2(acc, acc_c);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double s2 = 0.0, s1 = 0.0;
+      for (int k = threadIdx.x; k < kSplitThreads; k += 32) {
+        s2 += red[k].x;
+        s1 += red[k].y;
       }
-    } else if (threadIdx.x == 0) {
-      part[slot] = s;
+      for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      }
+      if (threadIdx.x == 0) {
+        const size_t slot = (size_t)row * gridDim.x + blockIdx.x;
+        part[slot] = first_chunk ? s2 : part[slot] + s2;
+        part_c[slot] = first_chunk ? s1 : part_c[slot] + s1;
+      }
     }
+    __syncthreads();
   }
 }
 
-// ss_i = sum of the row's partials in a fixed order; rs_i = 1 / sqrt(ss_i)
-__global__ void vec_finalize_kernel(const double *__restrict__ part, int64_t row0, int64_t n,
-                                    int nparts, double *__restrict__ ss,
-                                    double *__restrict__ rs) {
-  for (int64_t lr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lr < n;
-       lr += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = row0 + lr;
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[row * nparts + b];
-    ss[row] = s;
-    // zero variance: correlation undefined, propagate NaN
-    rs[row] = s > 0.0 ? 1.0 / sqrt(s) : __longlong_as_double(0x7ff8000000000000ll);
+
+// The shift of each row: the FP64 mean of up to kShiftSamples values spread
+// evenly over the row; rows are centred on it in the single pass that
+// follows, and the exact mean enters at the end (delta_i = mu_i - s_i from
+// the same pass's sums).  One warp per row.
+constexpr int kShiftSamples = 1024;
+__global__ void vec_shift_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64_t ld,
+                                 double *__restrict__ shift) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t count = D < kShiftSamples ? D : kShiftSamples, stride = D / count;
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+       row += warps) {
+    const float *x = X + row * ld;
+    double acc = 0.0;
+    for (int64_t k = lane; k < count; k += 32) acc += (double)__ldg(x + k * stride);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) shift[row] = acc / (double)count;
   }
 }
+
+// A row whose shift misses its mean by D delta^2 > ss / 64 is centred again
+// on the exact mean: the shifted rows' common part D delta_i delta_j then
+// stays below 1/64 of sqrt(ss_i ss_j), so it adds nothing measurable to the
+// rounding of the Gram's FP32 chains.
+constexpr double kRecentreRatio = 1.0 / 64.0;
 
 // Column-sliced rows centred on shifts s_i: with S1 = sum_k c_ik and
 // S2 = sum_k c_ik^2 over all D columns (c = x - s), delta_i = mu_i - s_i =
 // S1 / D and ss_i = S2 - S1 delta_i (the shifted-data form of the variance).
+// list (optional): rows beyond kRecentreRatio get shift += delta and are
+// appended to list = [count, rows...].
 __global__ void slice_stats_kernel(const double *__restrict__ part,
                                    const double *__restrict__ part_c, int64_t n, int nparts,
                                    int64_t D, double *__restrict__ delta,
-                                   double *__restrict__ ss, double *__restrict__ rs) {
+                                   double *__restrict__ ss, double *__restrict__ rs,
+                                   double *__restrict__ shift, int32_t *__restrict__ list) {
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
        row += (int64_t)gridDim.x * blockDim.x) {
     double s1 = 0.0, s2 = 0.0;
@@ -212,6 +268,10 @@ __global__ void slice_stats_kernel(const double *__restrict__ part,
     delta[row] = d;
     ss[row] = v;
     rs[row] = v > 0.0 ? 1.0 / sqrt(v) : __longlong_as_double(0x7ff8000000000000ll);
+    if (list && v > 0.0 && (double)D * d * d > kRecentreRatio * v) {
+      shift[row] += d;
+      list[1 + atomicAdd(list, 1)] = (int32_t)row;
+    }
   }
 }
 
@@ -224,6 +284,18 @@ __global__ void slice_finalize_kernel(double *__restrict__ out, const double *__
     const int64_t p0 = pair_index(i, i + 1, n);
     for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x)
       out[p0 + (j - i - 1)] = (out[p0 + (j - i - 1)] - di * delta[j]) * (ri * rs[j]);
+  }
+}
+
+// r_ij -= (D delta_i rs_i)(delta_j rs_j): the same correction for pairs that
+// the whole-tile Gram epilogue already scaled by rs_i rs_j
+__global__ void pair_correct_kernel(double *__restrict__ out, const double *__restrict__ rs,
+                                    const double *__restrict__ delta, int64_t n, int64_t D) {
+  for (int64_t i = blockIdx.x; i < n - 1; i += gridDim.x) {
+    const double ei = (double)D * delta[i] * rs[i];
+    const int64_t p0 = pair_index(i, i + 1, n);
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x)
+      out[p0 + (j - i - 1)] -= ei * (delta[j] * rs[j]);
   }
 }
 
@@ -240,7 +312,8 @@ template <int COVER>
 __global__ void __launch_bounds__(256, 1)
 gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
                 const double *__restrict__ rs, const int32_t *__restrict__ tiles,
-                int64_t n_tiles, int32_t *queue, void *out) {
+                int64_t n_tiles, int32_t *queue, void *out, const double *__restrict__ delta,
+                double dcorr) {
   __shared__ __align__(16) float As[2][kF32K][kF32Tile + kF32Pad];
   __shared__ __align__(16) float Bs[2][kF32K][kF32Tile + kF32Pad];
   __shared__ int s_tile;
@@ -315,13 +388,16 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
       const int64_t i = i0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + (a - 4));
       if (i >= n) continue;
       const double ri = COVER ? 0.0 : rs[i];
+      const double di = (COVER || !delta) ? 0.0 : dcorr * delta[i];
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const int64_t j = j0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
         if (j >= n || j <= i) continue;
         const int64_t p = pair_index(i, j, n);
         if (COVER) atomicAdd(reinterpret_cast<int32_t *>(out) + p, 1);
-        else reinterpret_cast<double *>(out)[p] = (double)acc[a][b] * ri * rs[j];
+        else
+          reinterpret_cast<double *>(out)[p] =
+              ((double)acc[a][b] - (delta ? di * delta[j] : 0.0)) * ri * rs[j];
       }
     }
   }
@@ -339,25 +415,6 @@ cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_vec_split(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D, int64_t ld,
-                             int64_t Dp, const double *mu, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                             float *c32, double *part, double *ss, double *rs, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
-  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  if (vec4)
-    vec_split_kernel<true, false><<<grid, kSplitThreads, 0, s>>>(
-        X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32, part, nullptr, 1);
-  else
-    vec_split_kernel<false, false><<<grid, kSplitThreads, 0, s>>>(
-        X, row0, out_row0, n, D, ld, Dp, mu, hi, lo, c32, part, nullptr, 1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  vec_finalize_kernel<<<fg, 256, 0, s>>>(part, row0, n, kSplitParts, ss, rs);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_vec_split_slice(const float *X, int64_t row0, int64_t n, int64_t cols,
                                    int64_t ld, int64_t cols_p, const double *shift,
                                    __nv_bfloat16 *hi, __nv_bfloat16 *lo, double *part,
@@ -366,11 +423,67 @@ cudaError_t launch_vec_split_slice(const float *X, int64_t row0, int64_t n, int6
   dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
   const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   if (vec4)
-    vec_split_kernel<true, true><<<grid, kSplitThreads, 0, s>>>(
-        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk);
+    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk,
+        nullptr);
   else
-    vec_split_kernel<false, true><<<grid, kSplitThreads, 0, s>>>(
-        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk);
+    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk,
+        nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_prep(const float *X, int64_t row0, int64_t out_row0, int64_t n, int64_t D,
+                            int64_t ld, int64_t Dp, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                            float *c32, double *shift, double *part, double *part_c,
+                            double *delta, double *ss, double *rs, int32_t *recentre,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int sg = (int)std::min<int64_t>((n + 7) / 8, 65535);
+  vec_shift_kernel<<<sg, 256, 0, s>>>(X, n, D, ld, shift + row0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  auto split = [&](dim3 grid, const int32_t *list) {
+    if (vec4)
+      vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(
+          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list);
+    else
+      vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(
+          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list);
+    return cudaGetLastError();
+  };
+  const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  auto stats = [&](int32_t *list) {
+    slice_stats_kernel<<<fg, 256, 0, s>>>(part + row0 * kSplitParts, part_c + row0 * kSplitParts,
+                                          n, kSplitParts, D, delta + row0, ss + row0, rs + row0,
+                                          shift + row0, list);
+    return cudaGetLastError();
+  };
+  if ((e = split(dim3(kSplitParts, (unsigned)(n < 65535 ? n : 65535)), nullptr)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(recentre, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  if ((e = stats(recentre)) != cudaSuccess) return e;
+  // the rows the sampled shift served badly, again from the exact mean (the
+  // list is normally empty and the CTAs return at once)
+  if ((e = split(dim3(kSplitParts, (unsigned)(n < 256 ? n : 256)), recentre)) != cudaSuccess)
+    return e;
+  return stats(nullptr);
+}
+
+cudaError_t launch_pair_correct(double *out, const double *rs, const double *delta, int64_t n,
+                                int64_t D, cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  const int grid = (int)(n - 1 < 65535 ? n - 1 : 65535);
+  pair_correct_kernel<<<grid, 256, 0, s>>>(out, rs, delta, n, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_finalize(double *out, const double *rs, const double *delta, int64_t n,
+                                 int64_t D, cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  const int grid = (int)(n - 1 < 65535 ? n - 1 : 65535);
+  slice_finalize_kernel<<<grid, 256, 0, s>>>(out, rs, delta, n, D);
   return cudaGetLastError();
 }
 
@@ -379,7 +492,8 @@ cudaError_t launch_slice_finalize(const double *part, const double *part_c, int6
                                   cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  slice_stats_kernel<<<fg, 256, 0, s>>>(part, part_c, n, kSplitParts, D, delta, ss, rs);
+  slice_stats_kernel<<<fg, 256, 0, s>>>(part, part_c, n, kSplitParts, D, delta, ss, rs, nullptr,
+                                        nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || n < 2) return e;
   const int grid = (int)(n - 1 < 65535 ? n - 1 : 65535);
@@ -389,16 +503,19 @@ cudaError_t launch_slice_finalize(const double *part, const double *part_c, int6
 
 cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double *rs,
                             const int32_t *tiles, int64_t n_tiles, int32_t *queue, void *out,
-                            int coverage, int64_t, int64_t, cudaStream_t s) {
+                            int coverage, int64_t, int64_t, cudaStream_t s, const double *delta,
+                            int64_t D) {
   if (n_tiles <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   int64_t grid = (int64_t)num_sms();
   if (grid > n_tiles) grid = n_tiles;
   if (coverage)
-    gram_f32_kernel<1><<<(int)grid, 256, 0, s>>>(C, n, Dp, rs, tiles, n_tiles, queue, out);
+    gram_f32_kernel<1><<<(int)grid, 256, 0, s>>>(C, n, Dp, rs, tiles, n_tiles, queue, out, delta,
+                                                 (double)D);
   else
-    gram_f32_kernel<0><<<(int)grid, 256, 0, s>>>(C, n, Dp, rs, tiles, n_tiles, queue, out);
+    gram_f32_kernel<0><<<(int)grid, 256, 0, s>>>(C, n, Dp, rs, tiles, n_tiles, queue, out, delta,
+                                                 (double)D);
   return cudaGetLastError();
 }
 

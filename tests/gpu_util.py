@@ -11,6 +11,23 @@ OVERLAP_BOUND_FACTOR = 3.0
 PEARSON_ATOL = 1e-6
 
 
+def shifted_rows(X):
+    """The rows as the vector pipeline feeds them to the Gram: centred on a
+    per-row shift s_i (the mean of min(D, 1024) values at stride
+    floor(D / count)), not on the mean; the exact mean enters afterwards as
+    r_ij = (G_ij - D delta_i delta_j) / sqrt(ss_i ss_j), delta = mean - s.
+    Rows with D delta^2 > ss / 64 are centred again on their mean.  The
+    products whose rounding the allowances bound are those of these rows."""
+    X = np.asarray(X, np.float64)
+    D = X.shape[1]
+    count = min(D, 1024)
+    s = X[:, : count * (D // count): D // count].mean(1, keepdims=True)
+    mu = X.mean(1, keepdims=True)
+    ss = ((X - mu) ** 2).sum(1, keepdims=True)
+    again = D * (mu - s) ** 2 > ss / 64
+    return X - np.where(again, mu, s)
+
+
 def pearson_tolerance(X, pi, pj, prec):
     """Per-pair error allowance of the GPU paths for short vectors.
 
@@ -21,18 +38,21 @@ def pearson_tolerance(X, pi, pj, prec):
     sqrt(sum_k c_ik^2 c_jk^2), divided by sqrt(ss_i ss_j).  It falls like
     1/sqrt(D) and is far below 1e-6 at D = 2^20.
     FP32: round-to-nearest accumulation over D terms, a random walk of
-    relative size ~2^-24 sqrt(D); allowance 2^-22 sqrt(D) |r|.
+    relative size ~2^-24 sqrt(D); allowance 2^-22 sqrt(D) |G_ij| /
+    sqrt(ss_i ss_j) (|r| for rows centred on their exact means).
+    c here are the shifted rows (see shifted_rows); ss the centred sums.
     """
     X = np.asarray(X, np.float64)
     C = X - X.mean(1, keepdims=True)
     ss = (C * C).sum(1)
+    Cs = shifted_rows(X)
     D = X.shape[1]
     if prec == 1:
-        S2 = C * C
+        S2 = Cs * Cs
         num = np.sqrt(np.einsum("pk,pk->p", S2[pi], S2[pj]))
         return PEARSON_ATOL + 6 * 2.0 ** -16 * num / np.sqrt(ss[pi] * ss[pj])
-    r = np.einsum("pk,pk->p", C[pi], C[pj]) / np.sqrt(ss[pi] * ss[pj])
-    return PEARSON_ATOL + 2.0 ** -22 * np.sqrt(D) * np.abs(r)
+    g = np.einsum("pk,pk->p", Cs[pi], Cs[pj]) / np.sqrt(ss[pi] * ss[pj])
+    return PEARSON_ATOL + 2.0 ** -22 * np.sqrt(D) * np.abs(g)
 def regroup_tolerance(X, pi, pj, chain=256):
     """Allowance between two split-BF16 results that differ only in how the
     same products are grouped into tensor-core chains (whole tiles against
@@ -44,13 +64,15 @@ def regroup_tolerance(X, pi, pj, chain=256):
     for a chain whose |products| sum to S_c.  Chains round independently, so
     one result is off by about 2^-23 sqrt(3 chain) sqrt(sum_c S_c^2); two
     results, and a factor 4 for the tail: 8 * 2^-23 sqrt(3 chain)
-    sqrt(sum_c S_c^2) / sqrt(ss_i ss_j).  A lost or doubled 64-column range
+    sqrt(sum_c S_c^2) / sqrt(ss_i ss_j), the products those of the shifted
+    rows (see shifted_rows).  A lost or doubled 64-column range
     moves r by about its share of sum |c_i c_j|, orders of magnitude more.
     """
     X = np.asarray(X, np.float64)
-    C = np.abs(X - X.mean(1, keepdims=True))
+    C = np.abs(shifted_rows(X))
     n, D = C.shape
-    ss = (C * C).sum(1)
+    Cm = X - X.mean(1, keepdims=True)
+    ss = (Cm * Cm).sum(1)
     nc = (D + chain - 1) // chain
     Cp = np.zeros((n, nc * chain))
     Cp[:, :D] = C

@@ -224,3 +224,58 @@ def test_pearson_correlated_bias(ap, oracle_lib, k_split):
     assert np.abs(ref).min() > 0.99
     assert abs(d[ref > 0].mean()) <= 3e-7 and abs(d[ref < 0].mean()) <= 3e-7
     assert np.abs(d).max() <= PEARSON_ATOL
+
+
+def _offset_trend_rows(n, D, seed):
+    """Grouped rows plus large per-row offsets (up to 1e4 times the spread),
+    linear trends, and rows periodic with period 12, the sampling stride of
+    the shift at D = 12325 (every sample falls on the same phase, so the
+    shift misses the mean by the full amplitude)."""
+    g = torch.Generator().manual_seed(seed)
+    X = synth.vectors_grouped(n, D, seed=seed).double()
+    k = torch.arange(D, dtype=torch.float64)
+    off = 1e4 * (2 * torch.rand(n, 1, generator=g, dtype=torch.float64) - 1)
+    off[::3] *= 1e-3
+    X += off
+    trend = torch.rand(n, 1, generator=g, dtype=torch.float64) * torch.linspace(-3, 3, D,
+                                                                                dtype=torch.float64)
+    X[1::3] += trend[1::3]
+    X[2::7] += 2.0 * torch.cos(2 * np.pi * k / 12)
+    return X.float().contiguous()
+
+
+def test_pearson_offsets_and_trends(ap, oracle_lib):
+    """Rows centred on a sampled shift in one pass: the exact mean enters as
+    the correction D delta_i delta_j; every path that prepares rows (device
+    and host sources, whole tiles and split-K, FP32, out-of-core macros in
+    both orders, load-and-run) must match the oracle on rows whose means,
+    trends and stride-aligned periods would expose a wrong correction."""
+    n, D = 300, 12325
+    X = _offset_trend_rows(n, D, seed=17)
+    Xn = X.numpy()
+    pi, pj = oracle_lib.all_pairs(n)
+    ref = oracle_lib.pearson(Xn, pi, pj)
+    tol = pearson_tolerance(Xn, pi, pj, 1)
+    tol32 = pearson_tolerance(Xn, pi, pj, 0)
+
+    def check(got, t, what):
+        err = np.abs(got - ref)
+        assert np.all(err <= t), f"{what}: max |err| {err.max():.3e}, worst {(err / t).max():.2f}x"
+
+    both = (ap.AP_PREC_SPLIT_BF16, ap.AP_PREC_FP32)
+    with ap.Items.from_vectors(X.cuda(), precisions=both) as it:
+        for k in (0, -1, 3):
+            it.set_plan(128, 256, 0, k)
+            check(it.run_pairs().cpu().numpy(), tol, f"device k_split {k}")
+        check(it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32).cpu().numpy(), tol32, "fp32")
+        assert it.last_device_error() == 0
+    check(_run(ap, X, ap.AP_PREC_SPLIT_BF16, host=True), tol, "host source")
+    Xp = X.pin_memory()
+    cache = 3 * 256 * ((D + 63) // 64 * 64) * 4
+    with ap.Items.from_vectors(Xp, slot_cache_bytes=cache) as it:
+        check(it.run_pairs().cpu().numpy(), tol, "out-of-core resident+streamed")
+        it.set_out_of_core_policy(ap.binding.AP_OOC_DC_LRU)
+        check(it.run_pairs().cpu().numpy(), tol, "out-of-core recursive+LRU")
+        assert it.last_device_error() == 0
+    with ap.Items.from_vectors(Xp) as it:
+        check(it.load_and_run(Xp).cpu().numpy(), tol, "load and run")
