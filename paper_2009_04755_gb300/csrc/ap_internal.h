@@ -208,6 +208,9 @@ struct SparseStore {
   double *d_rs = nullptr;           // 1 / sqrt(sum of squares), NaN for none
   int32_t *d_tiles = nullptr;       // block pairs (I <= J) of 32 items
   int64_t n_tiles = 0;
+  // per block of 32 items: the item (0..31) each row slot j of a tile takes;
+  // slots w and w + 16 (one warp) pair a heavy row with a light one
+  int32_t *d_jperm = nullptr;
 };
 }  // namespace ap
 

@@ -9,12 +9,18 @@
 // Schedule: persistent CTAs pop tiles (a block of 32 items I x a block of 32
 // items J, upper triangle in recursive quadrant order, Sec. IV-B) from an
 // atomic queue.  The 16 warps walk the chunks together, for half of I (16
-// rows) at a time: per chunk each warp scatters one row i into its dense
-// array of the chunk in shared memory, and after a barrier every lane reads
+// rows) at a time: per chunk each warp scatters one row i into the dense
+// form of the chunk in shared memory, and after a barrier every lane reads
 // its share of the chunk's entries of the warp's two rows j (once, into
-// registers) and multiplies each against the 16 dense arrays -- a product
-// costs one shared-memory gather, the entry reads are shared by 16 rows i.
-// Each warp copies the next chunk's entries of its rows (up to 64 per row)
+// registers) and multiplies each against the 16 rows i.  The dense form is
+// code-major, the 16 rows' values of one code side by side (64 bytes), so
+// one 16-byte load gathers four rows; the four 16-byte groups of a code are
+// XOR-swizzled by code bits 1-2, which spreads the loads of random codes
+// over all eight 16-byte bank groups.
+// The barriers pace every chunk step by its busiest warp, so the rows j of a
+// block are dealt to the warps in pairs of one heavy and one light row (by
+// entry count).  Each warp copies the next chunk's entries of its rows (up to
+// 64 per row)
 // into a two-stage shared-memory ring with cp.async while it works on the
 // current one, so the chunk loop does not wait on DRAM.  Per lane the FP32
 // products are summed over up to 64 chunks, then folded into FP64 pair sums
@@ -23,6 +29,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ap_internal.h"
@@ -39,6 +46,11 @@ constexpr int kMinBlocks = 16 / kWarps;      // CTAs per SM the registers are si
 constexpr int kStage = 64;                   // staged entries per row and chunk
 constexpr int W = kSparseChunk;
 constexpr int kFoldChunks = 64;
+
+// word of row q (0..kWarps-1) at chunk code k in the swizzled dense form
+__device__ __forceinline__ int dense_at(int k, int q) {
+  return k * kWarps + ((((q >> 2) ^ (k >> 1)) & 3) << 2) + (q & 3);
+}
 
 // asynchronous 4-byte copy global -> shared; src_bytes 0 writes zeros and
 // reads nothing
@@ -67,10 +79,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
 sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
                   const float *__restrict__ val, const int32_t *__restrict__ cptr,
                   const double *__restrict__ rs, int64_t n, int64_t n_chunks,
-                  const int32_t *__restrict__ tiles, int64_t n_tiles, int32_t *queue,
-                  void *out) {
+                  const int32_t *__restrict__ tiles, int64_t n_tiles,
+                  const int32_t *__restrict__ jperm, int32_t *queue, void *out) {
   extern __shared__ __align__(16) uint8_t smem[];
-  float *dense = reinterpret_cast<float *>(smem);                     // [kWarps][W]
+  float *dense = reinterpret_cast<float *>(smem);                     // [W][kWarps], swizzled
   double *s_g = reinterpret_cast<double *>(dense + kWarps * W);       // [B][B]
   WarpStage *stage = reinterpret_cast<WarpStage *>(s_g + B * B);      // [kWarps][2]
   __shared__ int s_tile;
@@ -85,6 +97,7 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     if (t >= n_tiles) break;
     const int64_t I = tiles[2 * t], J = tiles[2 * t + 1];
     const int64_t i0 = I * B, j0 = J * B;
+    const int32_t *jslot = jperm + J * B;     // item of each row slot of J
     const bool diag = I == J;
     for (int q = threadIdx.x; q < B * B; q += kThreads) s_g[q] = 0.0;
     __syncthreads();
@@ -92,23 +105,39 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     if (!COVER) {
       for (int pass = 0; pass < B / kWarps; ++pass) {
         // the warp's rows: r = 0 its row i (scattered into dense[warp]),
-        // r = 1.. its rows j (jl = warp + (r - 1) * kWarps)
+        // r = 1.. its rows j (slots warp + (r - 1) * kWarps, items jl)
         int64_t row[1 + kJ], base[1 + kJ];
+        int32_t jl[kJ];
         bool valid[1 + kJ];
         row[0] = i0 + pass * kWarps + warp;
 #pragma unroll
-        for (int h = 0; h < kJ; ++h) row[1 + h] = j0 + warp + h * kWarps;
+        for (int h = 0; h < kJ; ++h) {
+          jl[h] = jslot[warp + h * kWarps];
+          row[1 + h] = j0 + jl[h];
+        }
 #pragma unroll
         for (int r = 0; r <= kJ; ++r) {
           valid[r] = row[r] < n;
           base[r] = valid[r] ? off[row[r]] : 0;
         }
-        float *mine = dense + warp * W;
         float acc[kJ][kWarps];
 #pragma unroll
         for (int h = 0; h < kJ; ++h)
 #pragma unroll
           for (int q = 0; q < kWarps; ++q) acc[h][q] = 0.f;
+        // one entry (code k of the chunk, value v) of a row j against the 16
+        // rows i: four 16-byte loads of the dense form
+        auto product = [&](int32_t k, float v, float (&a)[kWarps]) {
+          const float4 *dk = reinterpret_cast<const float4 *>(dense + k * kWarps);
+#pragma unroll
+          for (int g = 0; g < kWarps / 4; ++g) {
+            const float4 d = dk[(g ^ (k >> 1)) & 3];
+            a[4 * g + 0] = fmaf(d.x, v, a[4 * g + 0]);
+            a[4 * g + 1] = fmaf(d.y, v, a[4 * g + 1]);
+            a[4 * g + 2] = fmaf(d.z, v, a[4 * g + 2]);
+            a[4 * g + 3] = fmaf(d.w, v, a[4 * g + 3]);
+          }
+        };
         int since = 0;
         // chunk starts b0..b3 = cptr of chunks c .. c + 3 (relative to the row)
         int32_t b0[1 + kJ], b1[1 + kJ], b2[1 + kJ], b3[1 + kJ];
@@ -149,10 +178,11 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
           const int32_t ni = b1[0] - b0[0];
 #pragma unroll
           for (int u = 0; u < kStage / 32; ++u)
-            if (u * 32 + lane < ni) mine[st.code[0][u * 32 + lane] - code0] = st.val[0][u * 32 + lane];
+            if (u * 32 + lane < ni)
+              dense[dense_at(st.code[0][u * 32 + lane] - code0, warp)] = st.val[0][u * 32 + lane];
           for (int32_t e = kStage + lane; e < ni; e += 32) {
             const int64_t g = base[0] + b0[0] + e;
-            mine[__ldg(idx + g) - code0] = __ldg(val + g);
+            dense[dense_at(__ldg(idx + g) - code0, warp)] = __ldg(val + g);
           }
           __syncthreads();
           // every entry of the warp's rows j in this chunk against the
@@ -161,31 +191,25 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
           for (int h = 0; h < kJ; ++h) {
             // on the diagonal, rows j at or before every row i of this pass
             // have no pair i < j here
-            if (!valid[1 + h] || (diag && warp + h * kWarps <= pass * kWarps)) continue;
+            if (!valid[1 + h] || (diag && jl[h] <= pass * kWarps)) continue;
             const int32_t nj = b1[1 + h] - b0[1 + h];
 #pragma unroll
             for (int u = 0; u < kStage / 32; ++u) {
-              if (u * 32 + lane < nj) {
-                const int32_t k = st.code[1 + h][u * 32 + lane] - code0;
-                const float v = st.val[1 + h][u * 32 + lane];
-#pragma unroll
-                for (int q = 0; q < kWarps; ++q) acc[h][q] = fmaf(dense[q * W + k], v, acc[h][q]);
-              }
+              if (u * 32 + lane < nj)
+                product(st.code[1 + h][u * 32 + lane] - code0, st.val[1 + h][u * 32 + lane],
+                        acc[h]);
             }
             for (int32_t e = kStage + lane; e < nj; e += 32) {
               const int64_t g = base[1 + h] + b0[1 + h] + e;
-              const int32_t k = __ldg(idx + g) - code0;
-              const float v = __ldg(val + g);
-#pragma unroll
-              for (int q = 0; q < kWarps; ++q) acc[h][q] = fmaf(dense[q * W + k], v, acc[h][q]);
+              product(__ldg(idx + g) - code0, __ldg(val + g), acc[h]);
             }
           }
           __syncthreads();
 #pragma unroll
           for (int u = 0; u < kStage / 32; ++u)
-            if (u * 32 + lane < ni) mine[st.code[0][u * 32 + lane] - code0] = 0.f;
+            if (u * 32 + lane < ni) dense[dense_at(st.code[0][u * 32 + lane] - code0, warp)] = 0.f;
           for (int32_t e = kStage + lane; e < ni; e += 32)
-            mine[__ldg(idx + base[0] + b0[0] + e) - code0] = 0.f;
+            dense[dense_at(__ldg(idx + base[0] + b0[0] + e) - code0, warp)] = 0.f;
 #pragma unroll
           for (int r = 0; r <= kJ; ++r) { b0[r] = b1[r]; b1[r] = b2[r]; b2[r] = b3[r]; }
           if (++since == kFoldChunks || c + 1 == n_chunks) {
@@ -207,8 +231,8 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     }
     __syncthreads();
     for (int q = threadIdx.x; q < B * B; q += kThreads) {
-      const int il = q / B, jl = q - il * B;
-      const int64_t i = i0 + il, j = j0 + jl;
+      const int il = q / B, slot = q - il * B;
+      const int64_t i = i0 + il, j = j0 + jslot[slot];
       if (i >= n || j >= n || j <= i) continue;
       const int64_t p = pair_index(i, j, n);
       if (COVER) atomicAdd(reinterpret_cast<int32_t *>(out) + p, 1);
@@ -270,6 +294,7 @@ void free_sparse(SparseStore &sp) {
   dfree(sp.d_cptr);
   dfree(sp.d_rs);
   dfree(sp.d_tiles);
+  dfree(sp.d_jperm);
 }
 
 ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
@@ -308,8 +333,28 @@ ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
     sparse_cptr_kernel<<<g2, 256, 0, s>>>(sp.d_off, sp.d_idx, sp.n, sp.n_chunks, sp.d_cptr);
     AP_TRY(cudaGetLastError());
   }
+  // row slots of each block: by entry count, slot w takes the w-th heaviest
+  // row and slot w + 16 the w-th lightest (rows past n count as empty)
+  const int64_t nblk = (sp.n + kSparseBlock - 1) / kSparseBlock;
+  std::vector<int32_t> jperm((size_t)std::max<int64_t>(nblk, 1) * kSparseBlock);
+  for (int64_t b = 0; b < nblk; ++b) {
+    int32_t order[kSparseBlock];
+    auto cnt = [&](int32_t l) {
+      const int64_t i = b * kSparseBlock + l;
+      return i < sp.n ? off[i + 1] - off[i] : (int64_t)-1;
+    };
+    for (int32_t l = 0; l < kSparseBlock; ++l) order[l] = l;
+    std::stable_sort(order, order + kSparseBlock,
+                     [&](int32_t a, int32_t c) { return cnt(a) > cnt(c); });
+    for (int w = 0; w < kWarps; ++w) {
+      jperm[(size_t)b * kSparseBlock + w] = order[w];
+      jperm[(size_t)b * kSparseBlock + w + kWarps] = order[kSparseBlock - 1 - w];
+    }
+  }
+  AP_TRY(dmalloc(&sp.d_jperm, jperm.size()));
+  AP_TRY(cudaMemcpyAsync(sp.d_jperm, jperm.data(), jperm.size() * 4, cudaMemcpyHostToDevice, s));
   std::vector<int32_t> tiles;
-  dc_block_pairs((sp.n + kSparseBlock - 1) / kSparseBlock, tiles);
+  dc_block_pairs(nblk, tiles);
   sp.n_tiles = (int64_t)tiles.size() / 2;
   AP_TRY(dmalloc(&sp.d_tiles, std::max<size_t>(tiles.size(), 2)));
   if (!tiles.empty())
@@ -329,7 +374,7 @@ cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverag
   const size_t smem = (size_t)kWarps * W * 4 + (size_t)B * B * 8 +
                       (size_t)kWarps * 2 * sizeof(WarpStage);
   void (*kern)(const int64_t *, const int32_t *, const float *, const int32_t *, const double *,
-               int64_t, int64_t, const int32_t *, int64_t, int32_t *, void *) =
+               int64_t, int64_t, const int32_t *, int64_t, const int32_t *, int32_t *, void *) =
       coverage ? sparse_cos_kernel<1> : sparse_cos_kernel<0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -337,7 +382,8 @@ cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverag
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>((int64_t)num_sms() * kMinBlocks, sp.n_tiles);
   kern<<<(int)grid, kThreads, smem, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.d_cptr, sp.d_rs, sp.n,
-                                         sp.n_chunks, sp.d_tiles, sp.n_tiles, queue, out);
+                                         sp.n_chunks, sp.d_tiles, sp.n_tiles, sp.d_jperm, queue,
+                                         out);
   return cudaGetLastError();
 }
 
