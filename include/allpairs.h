@@ -158,7 +158,8 @@ typedef struct ap_run_stats {
   uint64_t h2d_bytes;       /* bytes copied host -> device */
   double slot_hit_rate;     /* fraction of item requests served by a resident slot */
   int32_t tile_m, tile_n;   /* tile shape used (items x items) */
-  int32_t order;            /* 0 = recursive quadrant order, 1 = row panels */
+  int32_t order;            /* 0 = recursive quadrant order, 1 = row panels,
+                               2 = largest tiles first (point sets under 16 MB) */
   int32_t reserved;
   int64_t parsed_rows;      /* rows decoded by the parse stage during the run */
   double host_hit_rate;     /* second-level cache: requests served without decoding */

@@ -325,6 +325,10 @@ int64_t tc_grid(int64_t n_tiles);
 size_t tc_scratch_doubles(int64_t n_tiles);
 void free_tc_tensor_maps(void *tmap_hi, void *tmap_lo);
 void tc_tiles(int64_t n, std::vector<int32_t> &tiles);   // (I-block of 128, J-block of 256)
+// cloud tiles of a set whose points take under 16 MB: reordered largest
+// first (point pairs per tile); returns whether it reordered
+bool order_cloud_tiles(const std::vector<int32_t> &bstart, const std::vector<int64_t> &cnt,
+                       int64_t total_pts, std::vector<int32_t> &tiles);
 // split-K units of the tiles: waves of `group` tiles, column range-major
 // inside each wave (k_split ranges of the nchunks 64-column chunks)
 void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t group,

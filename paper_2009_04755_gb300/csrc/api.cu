@@ -105,6 +105,7 @@ ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
               bstart);
   std::vector<int32_t> tiles;
   dc_block_pairs((int64_t)bstart.size() - 1, tiles);
+  const bool largest_first = order_cloud_tiles(bstart, cnt, c.total_pts, tiles);
   dfree(c.d_bstart);
   dfree(c.d_tiles);
   AP_TRY(dmalloc(&c.d_bstart, bstart.size()));
@@ -120,7 +121,7 @@ ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
   it->stats.tiles = c.n_tiles;
   it->stats.tile_m = ch.block_items;
   it->stats.tile_n = ch.block_items;
-  it->stats.order = 0;
+  it->stats.order = largest_first ? 2 : 0;
   ++it->plan_version;
   return AP_OK;
 }

@@ -68,6 +68,32 @@ double tile_cost(const std::vector<int32_t> &bstart, const std::vector<int64_t> 
 }
 
 }  // namespace
+
+// A set whose points fit many times into L2 gains nothing from the quadrant
+// order's locality, but a queue of uneven tiles ends with a tail: such sets
+// pop their tiles largest first (the greedy longest-first rule), so the last
+// tiles taken are the small ones.
+constexpr int64_t kLargestFirstBytes = 16ll << 20;
+
+bool order_cloud_tiles(const std::vector<int32_t> &bstart, const std::vector<int64_t> &cnt,
+                       int64_t total_pts, std::vector<int32_t> &tiles) {
+  if (total_pts * (int64_t)(sizeof(float4) + sizeof(float)) > kLargestFirstBytes) return false;
+  const size_t nt = tiles.size() / 2;
+  std::vector<std::pair<double, int64_t>> key(nt);
+  for (size_t t = 0; t < nt; ++t) key[t] = {-tile_cost(bstart, cnt, tiles[2 * t], tiles[2 * t + 1]), (int64_t)t};
+  std::stable_sort(key.begin(), key.end(),
+                   [](const std::pair<double, int64_t> &a, const std::pair<double, int64_t> &b) {
+                     return a.first < b.first;
+                   });
+  std::vector<int32_t> out(tiles.size());
+  for (size_t t = 0; t < nt; ++t) {
+    out[2 * t] = tiles[2 * key[t].second];
+    out[2 * t + 1] = tiles[2 * key[t].second + 1];
+  }
+  tiles.swap(out);
+  return true;
+}
+
 }  // namespace ap
 
 using namespace ap;
@@ -185,6 +211,7 @@ extern "C" ap_status ap_tune(ap_items *it, int32_t mode, void *stream, ap_plan *
         std::vector<int32_t> bstart, tiles;
         make_blocks(c.h_poff, cnt, bi, bp, 32LL * rr, kOverlapMaxRowJobs, bstart);
         dc_block_pairs((int64_t)bstart.size() - 1, tiles);
+        order_cloud_tiles(bstart, cnt, c.total_pts, tiles);
         const int64_t nt = (int64_t)tiles.size() / 2;
         std::vector<double> cost(nt);
         double total = 0;
