@@ -60,6 +60,7 @@ struct CloudStore {
   int32_t *d_perm = nullptr;        // [n]
   // tile plan (rebuilt when the tuned parameters change)
   int32_t block_items = 0, block_pts = 0, reg_r = 0;
+  int32_t max_rj = 0;               // most row jobs (chunks of 32 reg_r points) of a block
   bool sorted = false;
   std::vector<int32_t> h_bstart;    // block b = storage items [bstart[b], bstart[b+1])
   int32_t *d_bstart = nullptr;
@@ -329,6 +330,9 @@ void tc_tiles(int64_t n, std::vector<int32_t> &tiles);   // (I-block of 128, J-b
 // first (point pairs per tile); returns whether it reordered
 bool order_cloud_tiles(const std::vector<int32_t> &bstart, const std::vector<int64_t> &cnt,
                        int64_t total_pts, std::vector<int32_t> &tiles);
+// the most row jobs (chunks of `chunk` points) any block of a cloud plan has
+int32_t max_row_jobs(const std::vector<int32_t> &bstart, const std::vector<int64_t> &cnt,
+                     int64_t chunk);
 // split-K units of the tiles: waves of `group` tiles, column range-major
 // inside each wave (k_split ranges of the nchunks 64-column chunks)
 void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t group,

@@ -114,6 +114,7 @@ ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
   if (!tiles.empty())
     AP_TRY(cudaMemcpy(c.d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
   c.h_bstart = bstart;
+  c.max_rj = max_row_jobs(bstart, cnt, 32LL * ch.reg_r);
   c.n_tiles = (int64_t)tiles.size() / 2;
   c.block_items = ch.block_items;
   c.block_pts = ch.block_pts;

@@ -96,6 +96,8 @@ struct Params {
   int32_t *queue;
   int32_t *status;
   int32_t stage_cap;     // points that fit the shared staging buffer
+  int32_t max_rj;        // row jobs of the largest block: rows of the partials
+  int32_t part_items;    // items of a block: columns of the partials
   // outputs / extra inputs
   float *out;            // FWD: f[P]; COVER: int32 counts[P]
   const float *params;   // [P][3] (theta, tx, ty) or NULL
@@ -118,7 +120,7 @@ overlap_kernel(Params P) {
   float4 *s_pts = reinterpret_cast<float4 *>(smem);
   float *s_lw = reinterpret_cast<float *>(s_pts + P.stage_cap);
   float *s_part = (DIM == 3 && HAS_W) ? s_lw + P.stage_cap : s_lw;
-  int16_t *s_rj_item = reinterpret_cast<int16_t *>(s_part + kMaxRowJobs * kMaxBlockItems * NV);
+  int16_t *s_rj_item = reinterpret_cast<int16_t *>(s_part + P.max_rj * P.part_items * NV);
   int16_t *s_rj_chunk = s_rj_item + kMaxRowJobs;
   int16_t *s_rj_first = s_rj_chunk + kMaxRowJobs;            // [kMaxBlockItems + 1]
   uint64_t *s_bar = reinterpret_cast<uint64_t *>(
@@ -151,7 +153,7 @@ overlap_kernel(Params P) {
           s_rj_first[i - c.i_begin] = (int16_t)nrj;
           const int64_t np = P.cnt[i];
           const int nch = (int)((np + CH - 1) / CH);
-          for (int ch = 0; ch < nch && nrj < kMaxRowJobs; ++ch) {
+          for (int ch = 0; ch < nch && nrj < P.max_rj; ++ch) {
             s_rj_item[nrj] = (int16_t)(i - c.i_begin);
             s_rj_chunk[nrj] = (int16_t)ch;
             ++nrj;
@@ -376,7 +378,7 @@ overlap_kernel(Params P) {
             }
           }
           if (lane == 0) {
-            float *dst = s_part + ((size_t)rj * kMaxBlockItems + jl) * NV;
+            float *dst = s_part + ((size_t)rj * P.part_items + jl) * NV;
             dst[0] = vF;
             if (MODE == GRAD) { dst[1] = vX; dst[2] = vY; dst[3] = vT; }
           }
@@ -399,7 +401,7 @@ overlap_kernel(Params P) {
       }
       double sF = 0.0, sX = 0.0, sY = 0.0, sT = 0.0;
       for (int rj = s_rj_first[il]; rj < s_rj_first[il + 1]; ++rj) {
-        const float *src = s_part + ((size_t)rj * kMaxBlockItems + jl) * NV;
+        const float *src = s_part + ((size_t)rj * P.part_items + jl) * NV;
         sF += (double)src[0];
         if (MODE == GRAD) { sX += (double)src[1]; sY += (double)src[2]; sT += (double)src[3]; }
       }
@@ -551,7 +553,7 @@ template <int DIM, bool HAS_W, int MODE, int SCORE = 0>
 cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s) {
   constexpr int NV = (MODE == GRAD) ? 4 : 1;
   size_t smem = (size_t)P.stage_cap * 16 + ((DIM == 3 && HAS_W) ? (size_t)P.stage_cap * 4 : 0) +
-                (size_t)kMaxRowJobs * kMaxBlockItems * NV * 4 +
+                (size_t)P.max_rj * P.part_items * NV * 4 +
                 (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
   void (*kern)(Params) = nullptr;
   switch (reg_r) {
@@ -586,6 +588,8 @@ Params base_params(const CloudStore &cs, int32_t *queue, int32_t *status) {
   P.queue = queue;
   P.status = status;
   P.stage_cap = cs.block_pts;
+  P.max_rj = cs.max_rj > 0 ? cs.max_rj : kMaxRowJobs;
+  P.part_items = cs.block_items > 0 ? cs.block_items : kMaxBlockItems;
   return P;
 }
 

@@ -65,6 +65,17 @@ void make_blocks(const std::vector<int64_t> &poff, const std::vector<int64_t> &c
   bstart.push_back((int32_t)n);
 }
 
+int32_t max_row_jobs(const std::vector<int32_t> &bstart, const std::vector<int64_t> &cnt,
+                     int64_t chunk) {
+  int64_t best = 1;
+  for (size_t b = 0; b + 1 < bstart.size(); ++b) {
+    int64_t jobs = 0;
+    for (int32_t i = bstart[b]; i < bstart[b + 1]; ++i) jobs += (cnt[i] + chunk - 1) / chunk;
+    best = std::max(best, jobs);
+  }
+  return (int32_t)std::min<int64_t>(best, kOverlapMaxRowJobs);
+}
+
 void tc_tiles(int64_t n, std::vector<int32_t> &tiles) {
   // macro grid of kTcTileN items; each macro pair (I <= J) holds two row
   // halves of kTcTileM items, kept when they contain some pair i < j.

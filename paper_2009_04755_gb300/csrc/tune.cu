@@ -247,6 +247,7 @@ extern "C" ap_status ap_tune(ap_items *it, int32_t mode, void *stream, ap_plan *
         cand.block_items = bi;
         cand.block_pts = bp;
         cand.reg_r = rr;
+        cand.max_rj = max_row_jobs(bstart, cnt, 32LL * rr);
         auto launch = [&]() {
           return mode == 0 ? launch_overlap(cand, nullptr, d_out, 0, it->d_queue, s)
                            : launch_overlap_grad_q(cand, it->d_queue, nullptr, nullptr, d_g, d_out,
