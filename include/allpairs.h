@@ -193,9 +193,14 @@ typedef struct ap_plan {
  * transfer to the GPU and pre-process there) into library-owned storage.
  *   Clouds: points are padded per item to a multiple of 4 with zero weight
  *   and stored as (x, y[, z], sigma^2, log2 w) in device memory.
- *   Vectors: per item mu_i and ss_i in FP64 (two passes), then the centred
- *   rows c = x - mu_i, stored as BF16 hi = rn(c), lo = rn(c - hi) for
- *   split-BF16 and/or as FP32 c for the FP32 path, rows padded with zeros.
+ *   Vectors: one pass over the rows: each row is centred on a shift s_i
+ *   close to its mean (the mean of 1024 evenly strided values), c = x - s_i,
+ *   stored as BF16 hi = rn(c), lo = rn(c - hi) for split-BF16 and/or as
+ *   FP32 c for the FP32 path, rows padded with zeros, while FP64 sums of c
+ *   and c^2 give delta_i = mu_i - s_i and ss_i = sum (x - mu_i)^2 exactly
+ *   (the correlation subtracts D delta_i delta_j from the Gram in FP64); a
+ *   row whose shift missed its mean by D delta^2 > ss / 64 is written again
+ *   centred on its mean.
  *   Sparse vectors: the CSR arrays copied, FP64 squared norms per row, and
  *   per column chunk of 2048 codes the first entry of every row in it.
  * Inputs may be freed when the call returns (after a stream synchronise),
