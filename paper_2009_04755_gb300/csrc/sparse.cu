@@ -141,36 +141,39 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
         int since = 0;
         // chunk starts b0..b3 = cptr of chunks c .. c + 3 (relative to the row)
         int32_t b0[1 + kJ], b1[1 + kJ], b2[1 + kJ], b3[1 + kJ];
-        auto bound = [&](int r, int64_t c) -> int32_t {
-          return (valid[r] && c <= n_chunks) ? cptr[c * n + row[r]] : 0;
+        auto bound = [&](int r, int64_t cn, bool in_range) -> int32_t {
+          return (valid[r] && in_range) ? cptr[cn + row[r]] : 0;   // cn = c * n
         };
-        // copies of chunk c's first kStage entries of every row into stage s
+        // copies of chunk c's first kStage entries of every row into stage s;
+        // slots past a row's entries are not copied (nothing reads them)
         auto stage_copy = [&](int64_t c, const int32_t *lo, const int32_t *hi, int s) {
 #pragma unroll
           for (int r = 0; r <= kJ; ++r) {
 #pragma unroll
             for (int u = 0; u < kStage / 32; ++u) {
               const int32_t e = lo[r] + u * 32 + lane;
-              const bool in = c < n_chunks && e < hi[r];
-              const int64_t g = in ? base[r] + e : 0;
-              cp_async4(&my_stage[s].code[r][u * 32 + lane], idx + g, in ? 4u : 0u);
-              cp_async4(&my_stage[s].val[r][u * 32 + lane], val + g, in ? 4u : 0u);
+              if (c < n_chunks && e < hi[r]) {
+                const int64_t g = base[r] + e;
+                cp_async4(&my_stage[s].code[r][u * 32 + lane], idx + g, 4u);
+                cp_async4(&my_stage[s].val[r][u * 32 + lane], val + g, 4u);
+              }
             }
           }
           cp_async_commit();
         };
 #pragma unroll
         for (int r = 0; r <= kJ; ++r) {
-          b0[r] = bound(r, 0);
-          b1[r] = bound(r, 1);
-          b2[r] = bound(r, 2);
+          b0[r] = bound(r, 0, true);
+          b1[r] = bound(r, n, 1 <= n_chunks);
+          b2[r] = bound(r, 2 * n, 2 <= n_chunks);
         }
         stage_copy(0, b0, b1, 0);
         for (int64_t c = 0; c < n_chunks; ++c) {
           const int32_t code0 = (int32_t)(c * W);
           const int s = (int)(c & 1);
+          const int64_t cn3 = (c + 3) * n;
 #pragma unroll
-          for (int r = 0; r <= kJ; ++r) b3[r] = bound(r, c + 3);
+          for (int r = 0; r <= kJ; ++r) b3[r] = bound(r, cn3, c + 3 <= n_chunks);
           stage_copy(c + 1, b1, b2, s ^ 1);            // the next chunk, in flight
           cp_async_wait_prev();                        // this chunk's copies landed
           const WarpStage &st = my_stage[s];
