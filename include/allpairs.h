@@ -243,6 +243,28 @@ ap_status ap_run_pairs(ap_items *items, int32_t fn, int32_t precision,
                        const float *params, void *out, void *stream);
 
 /*
+ * ap_run_pairs_list -- f(l(a), l(b)) for a chosen list of pairs only (the
+ * comparison stage of Sec. III on a subset): out[k] = f(pi[k], pj[k]).
+ *   pi, pj: HOST int32[n_pairs], original item ids, 0 <= a, b < n_items,
+ *        a != b, either order, repeats allowed (copied before the call
+ *        returns; the call synchronises `stream`).
+ *   fn = AP_FN_OVERLAP, AP_FN_GMM_L2, AP_FN_BHATTACHARYYA: clouds; out
+ *        device float[n_pairs]; params NULL or device float[n_pairs][3], the
+ *        transform applied to item pj[k] (2-D only).  A pair listed as
+ *        (a < b) gives the bits of ap_run_pairs at a's and b's packed index.
+ *   fn = AP_FN_PEARSON: resident vector sets; out device double[n_pairs];
+ *        precision selects the representation (built at creation); one warp
+ *        per pair, the Gram's three products per column in FP32, FP64 sums.
+ * Errors: AP_ERR_INVALID_ARG (fn/kind mismatch, an index out of range or a
+ * == b, NULL arrays with n_pairs > 0, params with other than 2-D clouds),
+ * AP_ERR_STATE (representation not built), AP_ERR_UNSUPPORTED (out-of-core
+ * or sparse sets, n_pairs > INT32_MAX), AP_ERR_CUDA.
+ */
+ap_status ap_run_pairs_list(ap_items *items, int32_t fn, int32_t precision, const int32_t *pi,
+                            const int32_t *pj, int64_t n_pairs, const float *params, void *out,
+                            void *stream);
+
+/*
  * ap_load_and_run -- ap_update_items from host memory fused with
  * ap_run_pairs(AP_FN_PEARSON, AP_PREC_SPLIT_BF16) on a resident vector set:
  * the host rows travel in 256-item macros on the library's copy stream, each
@@ -284,6 +306,21 @@ ap_status ap_backward(ap_items *items, const float *params, const float *grad_ou
  */
 ap_status ap_ascent(ap_items *items, float *params, int32_t n_steps, float eta,
                     float fmin, float *f_out, int32_t *flags, void *stream);
+
+/*
+ * ap_backward_list, ap_ascent_list -- ap_backward and ap_ascent on a chosen
+ * list of pairs (registration of selected pairs, Sec. V-C): pi, pj as for
+ * ap_run_pairs_list (host, original ids, the transform acting on pj[k]);
+ * params, grad_out, grad_params, f_out and flags are device arrays of
+ * n_pairs (x 3) entries indexed by list position.  Errors as for
+ * ap_backward / ap_ascent and ap_run_pairs_list.
+ */
+ap_status ap_backward_list(ap_items *items, const int32_t *pi, const int32_t *pj,
+                           int64_t n_pairs, const float *params, const float *grad_out,
+                           float *grad_params, float *f_out, void *stream);
+ap_status ap_ascent_list(ap_items *items, const int32_t *pi, const int32_t *pj, int64_t n_pairs,
+                         float *params, int32_t n_steps, float eta, float fmin, float *f_out,
+                         int32_t *flags, void *stream);
 
 /* ap_destroy -- free everything the handle owns; NULL is accepted.  Waits for
  * the handle's outstanding work on its streams first. */

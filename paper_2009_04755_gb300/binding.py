@@ -94,6 +94,9 @@ def lib():
             "ap_plan_out_of_core": (i32, [i64, i64, ctypes.c_uint64, i32, ctypes.POINTER(i64),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]),
             "ap_set_out_of_core_policy": (i32, [vp, i32]),
+            "ap_run_pairs_list": (i32, [vp, i32, i32, vp, vp, i64, vp, vp, vp]),
+            "ap_backward_list": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
+            "ap_ascent_list": (i32, [vp, vp, vp, i64, vp, i32, f32, f32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -334,6 +337,51 @@ class Items:
         check(lib().ap_run_pairs(self._h, fn, precision, _ptr(params), _ptr(out),
                                  _stream_ptr(stream)), "ap_run_pairs")
         return out[:self.P]
+
+    @staticmethod
+    def _pair_list(pi, pj):
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(pi, dtype=np.int32))
+        b = np.ascontiguousarray(np.asarray(pj, dtype=np.int32))
+        assert a.shape == b.shape and a.ndim == 1
+        return a, b
+
+    def run_pairs_list(self, pi, pj, fn: int = None, precision: int = AP_PREC_SPLIT_BF16,
+                       params=None, out=None, stream=None):
+        """f for the listed pairs (original item ids, host arrays):
+        out[k] = f(pi[k], pj[k]); a transform acts on pj[k]."""
+        import torch
+        a, b = self._pair_list(pi, pj)
+        if fn is None:
+            fn = AP_FN_PEARSON if self.kind == AP_ITEMS_VECTOR else AP_FN_OVERLAP
+        if out is None:
+            dt = torch.float64 if fn == AP_FN_PEARSON else torch.float32
+            out = torch.empty(max(len(a), 1), dtype=dt, device="cuda")
+        check(lib().ap_run_pairs_list(self._h, fn, precision, a.ctypes.data, b.ctypes.data,
+                                      len(a), _ptr(params), _ptr(out), _stream_ptr(stream)),
+              "ap_run_pairs_list")
+        return out[:len(a)]
+
+    def backward_list(self, pi, pj, params=None, grad_out=None, stream=None):
+        import torch
+        a, b = self._pair_list(pi, pj)
+        g = torch.empty(max(len(a), 1), 3, dtype=torch.float32, device="cuda")
+        f = torch.empty(max(len(a), 1), dtype=torch.float32, device="cuda")
+        check(lib().ap_backward_list(self._h, a.ctypes.data, b.ctypes.data, len(a), _ptr(params),
+                                     _ptr(grad_out), _ptr(g), _ptr(f), _stream_ptr(stream)),
+              "ap_backward_list")
+        return g[:len(a)], f[:len(a)]
+
+    def ascent_list(self, pi, pj, params, n_steps: int, eta: float, fmin: float = 1e-30,
+                    stream=None):
+        import torch
+        a, b = self._pair_list(pi, pj)
+        f = torch.empty(max(len(a), 1), dtype=torch.float32, device="cuda")
+        flags = torch.zeros(max(len(a), 1), dtype=torch.int32, device="cuda")
+        check(lib().ap_ascent_list(self._h, a.ctypes.data, b.ctypes.data, len(a), _ptr(params),
+                                   int(n_steps), float(eta), float(fmin), _ptr(f), _ptr(flags),
+                                   _stream_ptr(stream)), "ap_ascent_list")
+        return params, f[:len(a)], flags[:len(a)]
 
     def load_and_run(self, X_host, out=None, stream=None):
         """Load new host vectors and correlate all pairs, transfers overlapped

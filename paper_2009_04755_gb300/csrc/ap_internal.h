@@ -62,6 +62,13 @@ struct CloudStore {
   int32_t block_items = 0, block_pts = 0, reg_r = 0;
   int32_t max_rj = 0;               // most row jobs (chunks of 32 reg_r points) of a block
   bool sorted = false;
+  // pair lists: tiles are listed pairs of one-item blocks, outputs by list
+  // position (set only on the temporary copy a list run launches with)
+  bool list_mode = false;
+  std::vector<int32_t> h_iperm;     // original item id -> storage position
+  int32_t *d_bstart_single = nullptr;   // [n + 1]: block b = item b
+  int32_t *d_list_tiles = nullptr;  // [list_cap][2] storage positions
+  int64_t list_cap = 0;
   std::vector<int32_t> h_bstart;    // block b = storage items [bstart[b], bstart[b+1])
   int32_t *d_bstart = nullptr;
   int32_t *d_tiles = nullptr;       // [n_tiles][2] block pairs (I <= J)
@@ -341,6 +348,13 @@ void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t gro
 // ranges per tile (0 whole tiles, -1 the default rule of default_k_split)
 int32_t default_k_split(int64_t n_tiles, int64_t Dp);
 ap_status set_vector_plan(ap_items *it, int32_t k_split);
+
+// the particle scores' re-scaled cloud storage and L2 self terms, built on
+// first use (api.cu)
+ap_status ensure_score_storage(ap_items *it, int score, cudaStream_t s);
+// pair lists (pairlist.cu): Pearson of listed pairs over the resident rows
+cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
+                                const int32_t *pj, int64_t n_pairs, double *out, cudaStream_t s);
 
 // clouds (overlap.cu)
 cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,

@@ -46,7 +46,7 @@ void free_items(ap_items *it) {
   cudaDeviceSynchronize();          // queued host functions may still use the host cache
   CloudStore &c = it->cl;
   dfree(c.d_pts); dfree(c.d_lw); dfree(c.d_poff); dfree(c.d_cnt); dfree(c.d_perm);
-  dfree(c.d_bstart); dfree(c.d_tiles);
+  dfree(c.d_bstart); dfree(c.d_tiles); dfree(c.d_bstart_single); dfree(c.d_list_tiles);
   for (int k = 0; k < 2; ++k) { dfree(c.d_pts_score[k]); dfree(c.d_lw_score[k]); }
   dfree(c.d_self);
   VecStore &v = it->vec;
@@ -329,6 +329,21 @@ ap_status create_vectors(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
 }
 
 }  // namespace
+ap_status ensure_score_storage(ap_items *it, int score, cudaStream_t s) {
+  CloudStore &c = it->cl;
+  if (c.d_pts_score[score - 1]) return AP_OK;
+  // the re-scaled storage (and the L2 self terms) on first use
+  const bool lw = score == 2 ? c.dim == 3 : c.d_lw != nullptr;
+  AP_TRY(dmalloc(&c.d_pts_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
+  if (lw) AP_TRY(dmalloc(&c.d_lw_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
+  AP_TRY(launch_cloud_rescore(c, score, c.d_pts_score[score - 1], c.d_lw_score[score - 1], s));
+  if (score == 1) {
+    AP_TRY(dmalloc(&c.d_self, (size_t)c.n));
+    AP_TRY(launch_cloud_self(c, c.d_pts_score[0], c.d_lw_score[0], c.d_self, s));
+  }
+  return AP_OK;
+}
+
 }  // namespace ap
 
 using namespace ap;
@@ -490,18 +505,7 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   }
   if (fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA) {
     const int score = fn == AP_FN_GMM_L2 ? 1 : 2;
-    CloudStore &c = it->cl;
-    if (!c.d_pts_score[score - 1]) {
-      // the re-scaled storage (and the L2 self terms) on first use
-      const bool lw = score == 2 ? c.dim == 3 : c.d_lw != nullptr;
-      AP_TRY(dmalloc(&c.d_pts_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
-      if (lw) AP_TRY(dmalloc(&c.d_lw_score[score - 1], (size_t)std::max<int64_t>(c.total_pts, 1)));
-      AP_TRY(launch_cloud_rescore(c, score, c.d_pts_score[score - 1], c.d_lw_score[score - 1], s));
-      if (score == 1) {
-        AP_TRY(dmalloc(&c.d_self, (size_t)c.n));
-        AP_TRY(launch_cloud_self(c, c.d_pts_score[0], c.d_lw_score[0], c.d_self, s));
-      }
-    }
+    AP_TRY_ST(ensure_score_storage(it, score, s));
     GraphKey key{3 + score, params, out, nullptr, nullptr, 0.f, 0.f, 1};
     ap_items *h = it;
     ap_status st = run_graphed(it, key, s, [h, params, out, score](cudaStream_t cs) {
@@ -530,6 +534,7 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   it->stats.slot_hit_rate = 1.0;
   return AP_OK;
 }
+
 
 ap_status ap_backward(ap_items *it, const float *params, const float *grad_out,
                       float *grad_params, float *f_out, void *stream) {

@@ -98,6 +98,8 @@ struct Params {
   int32_t stage_cap;     // points that fit the shared staging buffer
   int32_t max_rj;        // row jobs of the largest block: rows of the partials
   int32_t part_items;    // items of a block: columns of the partials
+  int32_t list_mode;     // tiles are listed pairs: tile t's params and outputs
+                         // sit at index t (not at the packed pair index)
   // outputs / extra inputs
   float *out;            // FWD: f[P]; COVER: int32 counts[P]
   const float *params;   // [P][3] (theta, tx, ty) or NULL
@@ -266,7 +268,7 @@ overlap_kernel(Params P) {
           int64_t pidx = 0;
           if (MODE == FWD_T || MODE == GRAD) {
             const int oi = P.perm[i], oj = P.perm[j];
-            pidx = pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
+            pidx = P.list_mode ? (int64_t)t : pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
             const float *pp = (MODE == GRAD && P.params_io) ? P.params_io : P.params;
             if (pp) {
               const float th = pp[3 * pidx];
@@ -394,7 +396,8 @@ overlap_kernel(Params P) {
       if (diag && jl <= il) continue;
       const int i = c.i_begin + il, j = c.j_begin + jl;
       const int oi = P.perm[i], oj = P.perm[j];
-      const int64_t p = pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
+      const int64_t p =
+          P.list_mode ? (int64_t)t : pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
       if (MODE == COVER) {
         atomicAdd(reinterpret_cast<int32_t *>(P.out) + p, 1);
         continue;
@@ -590,6 +593,7 @@ Params base_params(const CloudStore &cs, int32_t *queue, int32_t *status) {
   P.stage_cap = cs.block_pts;
   P.max_rj = cs.max_rj > 0 ? cs.max_rj : kMaxRowJobs;
   P.part_items = cs.block_items > 0 ? cs.block_items : kMaxBlockItems;
+  P.list_mode = cs.list_mode ? 1 : 0;
   return P;
 }
 

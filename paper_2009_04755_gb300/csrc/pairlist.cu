@@ -1,0 +1,237 @@
+// pairlist.cu -- the pair function over a chosen list of pairs instead of the
+// whole upper triangle: the comparison stage of Sec. III on a subset, and the
+// per-pair registration of chosen pairs (Sec. V-C).
+//
+// Clouds reuse the all-pairs kernel: each listed pair (a, b) becomes a tile
+// of two one-item blocks (storage positions of a and b), and the kernel's
+// list mode puts tile t's transform and outputs at index t; the transform
+// acts on b, as it acts on the second item of a packed pair.  A pair listed
+// in packed order (a < b) therefore gets exactly the operations, and the
+// bits, of the all-pairs run.
+//
+// Vectors use one warp per listed pair over the resident centred rows (split
+// BF16 or FP32 copy), the same three products per column as the tensor-core
+// Gram, summed in FP32 over 64 column blocks per lane and in FP64 after:
+//   r_k = (sum_c c_a c_b - D delta_a delta_b) rs_a rs_b.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr int kListThreads = 256;
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kListThreads)
+pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *__restrict__ lo,
+                    const float *__restrict__ c32, int64_t Dp, const int32_t *__restrict__ pi,
+                    const int32_t *__restrict__ pj, int64_t n_pairs,
+                    const double *__restrict__ rs, const double *__restrict__ delta, int64_t D,
+                    double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_pairs;
+       k += warps) {
+    const int64_t a = pi[k], b = pj[k];
+    double acc = 0.0;
+    float part = 0.f;
+    if (SPLIT) {
+      // lane l takes column l of every 32-column block (64 contiguous bytes
+      // per row and block for the warp)
+      const int64_t nkb = Dp / kTcKBlock;
+      for (int64_t kb = 0; kb < nkb; ++kb) {
+        const int64_t col = kb * kTcKBlock + lane;
+        const size_t oa = blocked_offset(a, col, nkb, kTcKBlock);
+        const size_t ob = blocked_offset(b, col, nkb, kTcKBlock);
+        const float ha = __bfloat162float(hi[oa]), la = __bfloat162float(lo[oa]);
+        const float hb = __bfloat162float(hi[ob]), lb = __bfloat162float(lo[ob]);
+        part = fmaf(ha, hb, part);
+        part = fmaf(ha, lb, part);
+        part = fmaf(la, hb, part);
+        if ((kb & 63) == 63) {
+          acc += (double)part;
+          part = 0.f;
+        }
+      }
+    } else {
+      const int64_t nkb = Dp / kF32KBlock;
+      for (int64_t col = lane, m = 0; col < Dp; col += 32, ++m) {
+        const float ca = c32[blocked_offset(a, col, nkb, kF32KBlock)];
+        const float cb = c32[blocked_offset(b, col, nkb, kF32KBlock)];
+        part = fmaf(ca, cb, part);
+        if ((m & 63) == 63) {
+          acc += (double)part;
+          part = 0.f;
+        }
+      }
+    }
+    acc += (double)part;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[k] = (acc - (double)D * delta[a] * delta[b]) * rs[a] * rs[b];
+  }
+}
+
+// host checks shared by every list call: indices in range, a != b
+ap_status check_list(const ap_items *it, const int32_t *pi, const int32_t *pj, int64_t n_pairs,
+                     int64_t n) {
+  if (n_pairs < 0 || (n_pairs > 0 && (!pi || !pj))) return AP_ERR_INVALID_ARG;
+  if (n_pairs > INT32_MAX) return AP_ERR_UNSUPPORTED;   // tile indices are int32
+  for (int64_t k = 0; k < n_pairs; ++k)
+    if (pi[k] < 0 || pj[k] < 0 || pi[k] >= n || pj[k] >= n || pi[k] == pj[k])
+      return AP_ERR_INVALID_ARG;
+  (void)it;
+  return AP_OK;
+}
+
+// the temporary list plan of a cloud set: one-item blocks, the listed pairs
+// as tiles (storage positions), copied to the handle's list buffer on `s`
+ap_status cloud_list_plan(ap_items *it, const int32_t *pi, const int32_t *pj, int64_t n_pairs,
+                          cudaStream_t s, CloudStore &lc) {
+  CloudStore &c = it->cl;
+  if (c.h_iperm.size() != (size_t)c.n) {
+    c.h_iperm.assign((size_t)c.n, 0);
+    for (int64_t p = 0; p < c.n; ++p) c.h_iperm[c.h_perm[p]] = (int32_t)p;
+  }
+  std::vector<int32_t> single((size_t)c.n + 1);
+  for (int64_t b = 0; b <= c.n; ++b) single[b] = (int32_t)b;
+  if (!c.d_bstart_single) {
+    AP_TRY(dmalloc(&c.d_bstart_single, single.size()));
+    AP_TRY(cudaMemcpy(c.d_bstart_single, single.data(), single.size() * 4,
+                      cudaMemcpyHostToDevice));
+  }
+  if (c.list_cap < n_pairs) {
+    AP_TRY(cudaStreamSynchronize(s));              // the old list may still be read
+    dfree(c.d_list_tiles);
+    c.list_cap = 0;
+    AP_TRY(dmalloc(&c.d_list_tiles, (size_t)n_pairs * 2));
+    c.list_cap = n_pairs;
+  } else {
+    AP_TRY(cudaStreamSynchronize(s));
+  }
+  std::vector<int32_t> tiles((size_t)n_pairs * 2);
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    tiles[2 * k] = c.h_iperm[pi[k]];
+    tiles[2 * k + 1] = c.h_iperm[pj[k]];
+  }
+  AP_TRY(cudaMemcpy(c.d_list_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
+  std::vector<int64_t> cnt((size_t)c.n);
+  for (int64_t p = 0; p < c.n; ++p) cnt[p] = c.h_size[c.h_perm[p]];
+  lc = c;
+  lc.list_mode = true;
+  lc.d_bstart = c.d_bstart_single;
+  lc.d_tiles = c.d_list_tiles;
+  lc.n_tiles = n_pairs;
+  lc.block_items = 1;
+  lc.max_rj = max_row_jobs(single, cnt, 32LL * c.reg_r);
+  return AP_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
+                                const int32_t *pj, int64_t n_pairs, double *out, cudaStream_t s) {
+  if (n_pairs <= 0) return cudaSuccess;
+  const int64_t need = (n_pairs + (kListThreads / 32) - 1) / (kListThreads / 32);
+  const int grid = (int)std::min<int64_t>(need, (int64_t)num_sms() * 8);
+  if (split)
+    pearson_list_kernel<true><<<grid, kListThreads, 0, s>>>(v.d_hi, v.d_lo, nullptr, v.Dp, pi, pj,
+                                                            n_pairs, v.d_rs, v.d_delta_all, v.D,
+                                                            out);
+  else
+    pearson_list_kernel<false><<<grid, kListThreads, 0, s>>>(nullptr, nullptr, v.d_c32, v.Dp, pi,
+                                                             pj, n_pairs, v.d_rs, v.d_delta_all,
+                                                             v.D, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ap
+
+using namespace ap;
+
+extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precision,
+                                       const int32_t *pi, const int32_t *pj, int64_t n_pairs,
+                                       const float *params, void *out, void *stream) {
+  if (!it) return AP_ERR_INVALID_ARG;
+  if (precision != AP_PREC_FP32 && precision != AP_PREC_SPLIT_BF16) return AP_ERR_INVALID_ARG;
+  const bool cloud_fn = fn == AP_FN_OVERLAP || fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA;
+  const bool cloud = it->kind == AP_ITEMS_CLOUD2D || it->kind == AP_ITEMS_CLOUD3D;
+  if (cloud_fn != cloud && !(fn == AP_FN_PEARSON && it->kind == AP_ITEMS_VECTOR))
+    return AP_ERR_INVALID_ARG;
+  if (!cloud_fn && fn != AP_FN_PEARSON) return AP_ERR_INVALID_ARG;
+  if (params && it->kind != AP_ITEMS_CLOUD2D) return AP_ERR_INVALID_ARG;
+  const int64_t n = cloud ? it->cl.n : it->vec.n;
+  AP_TRY_ST(check_list(it, pi, pj, n_pairs, n));
+  if (n_pairs == 0) return AP_OK;
+  if (!out) return AP_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!cloud) {
+    VecStore &v = it->vec;
+    if (v.out_of_core) return AP_ERR_UNSUPPORTED;   // rows are not resident
+    const bool split = precision == AP_PREC_SPLIT_BF16;
+    if ((split && !v.d_hi) || (!split && !v.d_c32)) return AP_ERR_STATE;
+    int32_t *d_idx = nullptr;
+    AP_TRY(dmalloc(&d_idx, (size_t)n_pairs * 2));
+    cudaError_t e = cudaMemcpyAsync(d_idx, pi, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_idx + n_pairs, pj, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_pearson_list(v, split, d_idx, d_idx + n_pairs, n_pairs,
+                              reinterpret_cast<double *>(out), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the index buffer goes
+    dfree(d_idx);
+    return e == cudaSuccess ? AP_OK : from_cuda(e);
+  }
+  CloudStore lc;
+  AP_TRY_ST(cloud_list_plan(it, pi, pj, n_pairs, s, lc));
+  if (fn == AP_FN_OVERLAP)
+    AP_TRY(launch_overlap(lc, params, reinterpret_cast<float *>(out), 0, it->d_queue, s));
+  else {
+    const int score = fn == AP_FN_GMM_L2 ? 1 : 2;
+    AP_TRY_ST(ensure_score_storage(it, score, s));
+    const CloudStore &c = it->cl;
+    AP_TRY(launch_score(lc, score, c.d_pts_score[score - 1], c.d_lw_score[score - 1], c.d_self,
+                        params, reinterpret_cast<float *>(out), it->d_queue, s));
+  }
+  return AP_OK;
+}
+
+extern "C" ap_status ap_backward_list(ap_items *it, const int32_t *pi, const int32_t *pj,
+                                      int64_t n_pairs, const float *params,
+                                      const float *grad_out, float *grad_params, float *f_out,
+                                      void *stream) {
+  if (!it) return AP_ERR_INVALID_ARG;
+  if (it->kind != AP_ITEMS_CLOUD2D) return AP_ERR_INVALID_ARG;
+  AP_TRY_ST(check_list(it, pi, pj, n_pairs, it->cl.n));
+  if (n_pairs == 0) return AP_OK;
+  if (!grad_params) return AP_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CloudStore lc;
+  AP_TRY_ST(cloud_list_plan(it, pi, pj, n_pairs, s, lc));
+  AP_TRY(launch_overlap_grad_q(lc, it->d_queue, params, grad_out, grad_params, f_out, 0.f, 0.f,
+                               nullptr, nullptr, s));
+  return AP_OK;
+}
+
+extern "C" ap_status ap_ascent_list(ap_items *it, const int32_t *pi, const int32_t *pj,
+                                    int64_t n_pairs, float *params, int32_t n_steps, float eta,
+                                    float fmin, float *f_out, int32_t *flags, void *stream) {
+  if (!it) return AP_ERR_INVALID_ARG;
+  if (it->kind != AP_ITEMS_CLOUD2D || n_steps < 0) return AP_ERR_INVALID_ARG;
+  AP_TRY_ST(check_list(it, pi, pj, n_pairs, it->cl.n));
+  if (n_pairs == 0 || n_steps == 0) return AP_OK;
+  if (!params) return AP_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CloudStore lc;
+  AP_TRY_ST(cloud_list_plan(it, pi, pj, n_pairs, s, lc));
+  for (int32_t k = 0; k < n_steps; ++k)
+    AP_TRY(launch_overlap_grad_q(lc, it->d_queue, nullptr, nullptr, nullptr, f_out, eta, fmin,
+                                 params, flags, s));
+  return AP_OK;
+}
