@@ -255,10 +255,12 @@ ap_status ap_run_pairs(ap_items *items, int32_t fn, int32_t precision,
  *   fn = AP_FN_PEARSON: resident vector sets; out device double[n_pairs];
  *        precision selects the representation (built at creation); one warp
  *        per pair, the Gram's three products per column in FP32, FP64 sums.
+ *   fn = AP_FN_COSINE: sparse sets; out device double[n_pairs]; the two
+ *        rows' codes merged (FP32 products, FP64 sums).
  * Errors: AP_ERR_INVALID_ARG (fn/kind mismatch, an index out of range or a
  * == b, NULL arrays with n_pairs > 0, params with other than 2-D clouds),
  * AP_ERR_STATE (representation not built), AP_ERR_UNSUPPORTED (out-of-core
- * or sparse sets, n_pairs > INT32_MAX), AP_ERR_CUDA.
+ * sets, n_pairs > INT32_MAX), AP_ERR_CUDA.
  */
 ap_status ap_run_pairs_list(ap_items *items, int32_t fn, int32_t precision, const int32_t *pi,
                             const int32_t *pj, int64_t n_pairs, const float *params, void *out,

@@ -353,9 +353,10 @@ class Items:
         import torch
         a, b = self._pair_list(pi, pj)
         if fn is None:
-            fn = AP_FN_PEARSON if self.kind == AP_ITEMS_VECTOR else AP_FN_OVERLAP
+            fn = {AP_ITEMS_VECTOR: AP_FN_PEARSON, AP_ITEMS_SPARSE: AP_FN_COSINE}.get(
+                self.kind, AP_FN_OVERLAP)
         if out is None:
-            dt = torch.float64 if fn == AP_FN_PEARSON else torch.float32
+            dt = torch.float64 if fn in (AP_FN_PEARSON, AP_FN_COSINE) else torch.float32
             out = torch.empty(max(len(a), 1), dtype=dt, device="cuda")
         check(lib().ap_run_pairs_list(self._h, fn, precision, a.ctypes.data, b.ctypes.data,
                                       len(a), _ptr(params), _ptr(out), _stream_ptr(stream)),

@@ -13,6 +13,7 @@
 // BF16 or FP32 copy), the same three products per column as the tensor-core
 // Gram, summed in FP32 over 64 column blocks per lane and in FP64 after:
 //   r_k = (sum_c c_a c_b - D delta_a delta_b) rs_a rs_b.
+// Sparse rows merge their sorted codes (one CTA per pair).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -78,6 +79,51 @@ pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *_
   }
 }
 
+// Sparse rows (strictly increasing codes): one CTA per listed pair, each
+// thread merging an even slice of row a's entries against row b from the
+// first code of b at or after its slice (a binary search), so a pair costs
+// about nnz_a + nnz_b reads; FP32 products summed per thread in FP64.
+constexpr int kMergeThreads = 256;
+__global__ void __launch_bounds__(kMergeThreads)
+cosine_list_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
+                   const float *__restrict__ val, const double *__restrict__ rs,
+                   const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
+                   int64_t n_pairs, double *__restrict__ out) {
+  __shared__ double red[kMergeThreads / 32];
+  for (int64_t k = blockIdx.x; k < n_pairs; k += gridDim.x) {
+    const int64_t a = pi[k], b = pj[k];
+    const int64_t a0 = off[a], na = off[a + 1] - a0, b0 = off[b], nb = off[b + 1] - b0;
+    const int64_t per = (na + blockDim.x - 1) / blockDim.x;
+    const int64_t s0 = (int64_t)threadIdx.x * per, s1 = s0 + per < na ? s0 + per : na;
+    double acc = 0.0;
+    if (s0 < s1) {
+      // first entry of b whose code is >= the slice's first code
+      const int32_t c0 = idx[a0 + s0];
+      int64_t lo = 0, hi = nb;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (idx[b0 + mid] < c0) lo = mid + 1;
+        else hi = mid;
+      }
+      int64_t q = lo;
+      for (int64_t e = s0; e < s1 && q < nb; ++e) {
+        const int32_t code = idx[a0 + e];
+        while (q < nb && idx[b0 + q] < code) ++q;
+        if (q < nb && idx[b0 + q] == code) acc += (double)(val[a0 + e] * val[b0 + q]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      out[k] = t * rs[a] * rs[b];
+    }
+    __syncthreads();
+  }
+}
+
 // host checks shared by every list call: indices in range, a != b
 ap_status check_list(const ap_items *it, const int32_t *pi, const int32_t *pj, int64_t n_pairs,
                      int64_t n) {
@@ -133,6 +179,15 @@ ap_status cloud_list_plan(ap_items *it, const int32_t *pi, const int32_t *pj, in
   return AP_OK;
 }
 
+// the listed pairs' indices on the device (host arrays in, stream-ordered)
+ap_status device_pairs(const int32_t *pi, const int32_t *pj, int64_t n_pairs, cudaStream_t s,
+                       int32_t **d_idx) {
+  AP_TRY(dmalloc(d_idx, (size_t)n_pairs * 2));
+  AP_TRY(cudaMemcpyAsync(*d_idx, pi, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s));
+  AP_TRY(cudaMemcpyAsync(*d_idx + n_pairs, pj, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s));
+  return AP_OK;
+}
+
 }  // namespace
 
 cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
@@ -162,31 +217,44 @@ extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precisi
   if (precision != AP_PREC_FP32 && precision != AP_PREC_SPLIT_BF16) return AP_ERR_INVALID_ARG;
   const bool cloud_fn = fn == AP_FN_OVERLAP || fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA;
   const bool cloud = it->kind == AP_ITEMS_CLOUD2D || it->kind == AP_ITEMS_CLOUD3D;
-  if (cloud_fn != cloud && !(fn == AP_FN_PEARSON && it->kind == AP_ITEMS_VECTOR))
-    return AP_ERR_INVALID_ARG;
-  if (!cloud_fn && fn != AP_FN_PEARSON) return AP_ERR_INVALID_ARG;
+  const bool ok_kind = cloud ? cloud_fn
+                             : (it->kind == AP_ITEMS_VECTOR && fn == AP_FN_PEARSON) ||
+                                   (it->kind == AP_ITEMS_SPARSE && fn == AP_FN_COSINE);
+  if (!ok_kind) return AP_ERR_INVALID_ARG;
   if (params && it->kind != AP_ITEMS_CLOUD2D) return AP_ERR_INVALID_ARG;
-  const int64_t n = cloud ? it->cl.n : it->vec.n;
+  const int64_t n = cloud ? it->cl.n : it->kind == AP_ITEMS_SPARSE ? it->sp.n : it->vec.n;
   AP_TRY_ST(check_list(it, pi, pj, n_pairs, n));
   if (n_pairs == 0) return AP_OK;
   if (!out) return AP_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!cloud) {
-    VecStore &v = it->vec;
-    if (v.out_of_core) return AP_ERR_UNSUPPORTED;   // rows are not resident
+    const bool sparse = it->kind == AP_ITEMS_SPARSE;
     const bool split = precision == AP_PREC_SPLIT_BF16;
-    if ((split && !v.d_hi) || (!split && !v.d_c32)) return AP_ERR_STATE;
+    if (!sparse) {
+      const VecStore &v = it->vec;
+      if (v.out_of_core) return AP_ERR_UNSUPPORTED;   // rows are not resident
+      if ((split && !v.d_hi) || (!split && !v.d_c32)) return AP_ERR_STATE;
+    }
     int32_t *d_idx = nullptr;
-    AP_TRY(dmalloc(&d_idx, (size_t)n_pairs * 2));
-    cudaError_t e = cudaMemcpyAsync(d_idx, pi, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_idx + n_pairs, pj, (size_t)n_pairs * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = launch_pearson_list(v, split, d_idx, d_idx + n_pairs, n_pairs,
-                              reinterpret_cast<double *>(out), s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the index buffer goes
+    ap_status st = device_pairs(pi, pj, n_pairs, s, &d_idx);
+    cudaError_t e = cudaSuccess;
+    if (st == AP_OK) {
+      if (sparse) {
+        const SparseStore &sp = it->sp;
+        const int grid = (int)std::min<int64_t>(n_pairs, (int64_t)num_sms() * 8);
+        cosine_list_kernel<<<grid, kMergeThreads, 0, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.d_rs,
+                                                           d_idx, d_idx + n_pairs, n_pairs,
+                                                           reinterpret_cast<double *>(out));
+        e = cudaGetLastError();
+      } else {
+        e = launch_pearson_list(it->vec, split, d_idx, d_idx + n_pairs, n_pairs,
+                                reinterpret_cast<double *>(out), s);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the index buffer goes
+      st = e == cudaSuccess ? AP_OK : from_cuda(e);
+    }
     dfree(d_idx);
-    return e == cudaSuccess ? AP_OK : from_cuda(e);
+    return st;
   }
   CloudStore lc;
   AP_TRY_ST(cloud_list_plan(it, pi, pj, n_pairs, s, lc));

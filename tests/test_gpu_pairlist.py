@@ -142,6 +142,30 @@ def test_pearson_list_full_size_rows(ap, oracle_lib):
     assert np.abs(got - ref).max() <= PEARSON_ATOL
 
 
+def test_cosine_list(ap, oracle_lib):
+    off, idx, val = synth.sparse_cv(60, dim=200000, nnz=(20, 20000), common=3000, seed=8)
+    # rows of every size; row 7 emptied (its pairs are NaN)
+    rows = [idx[off[k]:off[k + 1]] for k in range(60)]
+    rows[7] = rows[7][:0]
+    vals = [val[off[k]:off[k + 1]] for k in range(60)]
+    vals[7] = vals[7][:0]
+    off2 = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    idx2, val2 = np.concatenate(rows), np.concatenate(vals)
+    pi, pj = _random_list(60, 500, seed=4)
+    pi[:5], pj[:5] = 7, np.arange(5)                  # the empty row: NaN
+    ref = oracle_lib.sparse_cosine(off2, idx2, val2, pi, pj)
+    with ap.Items.from_sparse(off2, idx2, val2, 200000) as it:
+        got = it.run_pairs_list(pi, pj).cpu().numpy()
+        full = it.run_pairs().cpu().numpy()
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan) and nan[:5].all()
+    mag = oracle_lib.sparse_cosine(off2, idx2, np.abs(val2), pi, pj)
+    tol = 2.0 ** -20 * np.nan_to_num(mag) + 1e-12
+    assert np.all(np.abs(got[~nan] - ref[~nan]) <= tol[~nan])
+    good = ~nan
+    np.testing.assert_allclose(got[good], full[_packed(pi, pj, 60)][good], rtol=0, atol=1e-6)
+
+
 def test_list_rejects_bad_pairs(ap):
     c = synth.clouds_uniform(n=10, dim=2, size=(5, 9), seed=1)
     with ap.Items.from_clouds(c) as it:
