@@ -117,6 +117,23 @@ def test_backward_and_ascent_list(ap, oracle_lib):
         assert it.last_device_error() == 0
 
 
+def test_autograd_list(ap, oracle_lib):
+    from paper_2009_04755_gb300.autograd import overlap_align_list
+    c = synth.clouds_templates(n=30, seed=6)
+    pi, pj = _random_list(30, 120, seed=8)
+    rng = np.random.default_rng(4)
+    prm = np.stack([rng.uniform(-0.3, 0.3, 120), rng.uniform(-0.05, 0.05, 120),
+                    rng.uniform(-0.05, 0.05, 120)], 1).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, 120)
+    f_ref, g_ref = oracle_lib.overlap_grad(c, pi, pj, prm.astype(np.float64))
+    with ap.Items.from_clouds(c) as it:
+        p = torch.from_numpy(prm).cuda().requires_grad_(True)
+        f = overlap_align_list(it, pi, pj, p)
+        (f * torch.from_numpy(w).float().cuda()).sum().backward()
+        grad = p.grad.cpu().numpy()
+    check_grad(grad, g_ref * w[:, None], cloud_wsum(c, pi, pj) * w)
+
+
 @pytest.mark.parametrize("prec", [1, 0])
 def test_pearson_list(ap, oracle_lib, prec):
     n, D = 300, 12325
