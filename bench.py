@@ -460,6 +460,78 @@ def run_ooc_workload(args):
     return 0
 
 
+def run_pearson_list_workload(args):
+    """Pearson of a chosen list of pairs: 20,000 random pairs (either
+    orientation) of the resident 8192 x 2^20 set, one warp per pair over the
+    split-BF16 rows.  Random pairs share no rows worth caching, so each reads
+    both rows' hi and lo from HBM: the roofline is HBM bytes."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2009_04755_gb300 as ap
+    torch.cuda.set_device(0)
+    n, D = args.n or N_ITEMS, args.dim or DIM
+    L = 20000
+    X = synth.vectors_grouped(n, D, seed=0, device="cuda")
+    items = ap.Items.from_vectors(X, precisions=(ap.AP_PREC_SPLIT_BF16,))
+    rng = np.random.default_rng(11)
+    pi = rng.integers(0, n, L).astype(np.int32)
+    pj = ((pi + rng.integers(1, n, L)) % n).astype(np.int32)
+    out = torch.empty(L, dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        items.run_pairs_list(pi, pj, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        items.run_pairs_list(pi, pj, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    Dp = (D + 63) // 64 * 64
+    bytes_step = L * 2 * Dp * 4                       # both rows' hi + lo per pair
+    pk, pk_kind = peaks()
+    peak = pk.get("hbm_gbs", 6800.0)
+    gbs = bytes_step / (ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": L / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
+            "config": {"workload": f"pearson_list_n{n}_d{D}", "n_items": n, "dim": D,
+                       "listed_pairs": L, "precision": "split-bf16",
+                       "l2": "each step reads 168 GB of rows, far larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "kernel": "pearson_list_kernel",
+                         "peak_kind": f"{pk_kind} HBM copy",
+                         "algorithmic_bytes_per_step": bytes_step},
+            "gpu_launches": args.steps}
+    if clk:
+        line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if not args.no_cpu:
+        import oracle
+        k = 200
+        rows = np.unique(np.concatenate([pi[:k], pj[:k]]))
+        sub = X[torch.from_numpy(rows).cuda()].cpu().numpy()
+        remap = {r: q for q, r in enumerate(rows)}
+        cores = os.cpu_count() or 1
+        oracle.build()
+        t0 = time.perf_counter()
+        ref = oracle.pearson(sub, [remap[a] for a in pi[:k]], [remap[b] for b in pj[:k]],
+                             n_threads=cores)
+        secs = time.perf_counter() - t0
+        line["max_abs_err_sampled"] = float(np.abs(out[:k].cpu().numpy() - ref).max())
+        line["cpu_baseline"] = {"value": k / secs, "unit": "pairs/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"the first {k} listed pairs (their rows' statistics "
+                                          "included)"}
+    items.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 SPARSE_N, SPARSE_DIM = 2500, 20 ** 6
 # shared-memory / L1 data path of an SM: 128 bytes per clock; a probe of the
 # sparse cosine moves 12 (a 4-byte gather from the dense chunk + the 8-byte
@@ -645,14 +717,25 @@ def run_cloud_workload(args):
                                    sigma=(0.01, 0.03), seed=0)
     elif wl == "overlap3d_n20000":
         c = synth.clouds_lognormal(n=args.n or 20000, dim=3, seed=0)
-    else:
+    else:   # register2d_n1024 and its pair-list form
         c = synth.clouds_templates(n=1024, seed=0)
     n = len(c["offsets"]) - 1
     P = n * (n - 1) // 2
     sizes = np.diff(c["offsets"]).astype(np.float64)
     point_pairs = (sizes.sum() ** 2 - (sizes ** 2).sum()) / 2
+    listed = wl == "register2d_n1024_list"
+    if listed:
+        # a seeded quarter of the pairs, in random order and either orientation
+        rng = np.random.default_rng(7)
+        li, lj = np.triu_indices(n, 1)
+        keep = rng.permutation(P)[:P // 4]
+        flip = rng.random(len(keep)) < 0.5
+        lpi = np.where(flip, lj[keep], li[keep]).astype(np.int32)
+        lpj = np.where(flip, li[keep], lj[keep]).astype(np.int32)
+        P = len(keep)
+        point_pairs = float((sizes[lpi] * sizes[lpj]).sum())
     items = ap.Items.from_clouds(c)
-    reg = wl in ("register2d_n1024", "register_particles2d_n256")
+    reg = wl in ("register2d_n1024", "register_particles2d_n256", "register2d_n1024_list")
     if args.plan:
         bi, bp, rr = (int(v) for v in args.plan.split(","))
         items.set_plan(bi, bp, rr)
@@ -668,7 +751,10 @@ def run_cloud_workload(args):
           "bhattacharyya": ap.AP_FN_BHATTACHARYYA}[args.fn]
 
     def step():
-        if reg:
+        if listed:
+            prm.zero_()
+            items.ascent_list(lpi, lpj, prm, n_asc, 1e-3)
+        elif reg:
             prm.zero_()
             items.ascent(prm, n_asc, 1e-3)
             if wl == "register_particles2d_n256":
@@ -690,7 +776,7 @@ def run_cloud_workload(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     evals = n_asc + (wl == "register_particles2d_n256") if reg else 1   # pair evaluations per step
-    units = P * (n_asc if wl == "register2d_n1024" else 1)
+    units = P * (n_asc if wl in ("register2d_n1024", "register2d_n1024_list") else 1)
     mufu = 2.0 * point_pairs * evals
     sm_mhz = clk["sm_mhz"] if clk else 2070.0
     # one rcp (16/clk/SM) and one ex2 (32/clk/SM) per point pair: 2 MUFU
@@ -698,7 +784,7 @@ def run_cloud_workload(args):
     peak = 2.0 / (1.0 / RCP_PER_CLK_PER_SM + 1.0 / EX2_PER_CLK_PER_SM) * 152 * sm_mhz * 1e6 / 1e12
     achieved = mufu / (ms / 1e3) / 1e12
     line = {"metric": METRIC, "value": units / (ms / 1e3),
-            "unit": {"register2d_n1024": "pair-steps/s",
+            "unit": {"register2d_n1024": "pair-steps/s", "register2d_n1024_list": "pair-steps/s",
                      "register_particles2d_n256": "pair registrations/s"}.get(wl, "pairs/s"),
             "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -706,6 +792,8 @@ def run_cloud_workload(args):
             "config": {"workload": f"overlap3d_n{n}" if wl == "overlap3d_n20000" else wl,
                        "n_items": n, "pairs": P, "point_pairs": point_pairs,
                        "pair_function": {"register2d_n1024": "ascent (20 steps)",
+                                         "register2d_n1024_list":
+                                             "ascent (20 steps) on a listed quarter of the pairs",
                                          "register_particles2d_n256":
                                              "ascent (20 steps) + gmm_l2"}.get(wl, args.fn),
                        "plan": tuned},
@@ -726,10 +814,13 @@ def run_cloud_workload(args):
         pj = rng.integers(0, n, 4 * k)
         keep = pi < pj
         pi, pj = pi[keep][:k], pj[keep][:k]
+        if listed:                             # a sample of the listed pairs, as listed
+            sel = rng.permutation(P)[:k]
+            pi, pj = lpi[sel], lpj[sel]
         cores = os.cpu_count() or 1
         oracle.build()
         t0 = time.perf_counter()
-        if wl == "register2d_n1024":
+        if wl in ("register2d_n1024", "register2d_n1024_list"):
             f_ref, _ = oracle.overlap_grad(c, pi, pj, None, n_threads=cores)
         elif wl == "register_particles2d_n256":
             # one ascent evaluation on the sample, timed; the score at the
@@ -748,13 +839,16 @@ def run_cloud_workload(args):
             secs *= evals                      # the sample's time for a whole registration
             f_ref = oracle.gmm_l2(c, pi, pj, params=prm_s, n_threads=cores)
             items.run_pairs(ap.AP_FN_GMM_L2, params=prm, out=out)
-        else:
+        elif not listed:
             items.run_pairs(ap.AP_FN_OVERLAP if wl == "register2d_n1024" else fn, out=out)
-        p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
-        got = out[p].double().cpu().numpy()
+        if listed:
+            got = items.run_pairs_list(pi, pj).double().cpu().numpy()
+        else:
+            p = torch.from_numpy(pi * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+            got = out[p].double().cpu().numpy()
         line["max_rel_err_sampled"] = float((np.abs(got - f_ref) / np.abs(f_ref)).max())
         unit = line["unit"]
-        if wl == "register2d_n1024":
+        if wl in ("register2d_n1024", "register2d_n1024_list"):
             cpu_v, smp = len(pi) * n_asc / (secs * n_asc), "one ascent evaluation of"
         elif wl == "register_particles2d_n256":
             cpu_v, smp = len(pi) / secs, f"one ascent evaluation (x{evals}) of"
@@ -775,7 +869,8 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--workload", default="pearson_n8192_d1048576",
                     choices=["pearson_n8192_d1048576", "overlap2d_n256", "overlap3d_n20000",
-                             "register2d_n1024", "pearson_ooc_n8192_d3145728",
+                             "register2d_n1024", "register2d_n1024_list",
+                             "pearson_list_n8192_d1048576", "pearson_ooc_n8192_d3145728",
                              "particles2d_n256", "register_particles2d_n256",
                              "cosine_sparse_n2500", "pearson_encoded_n2048_d1048576"])
     ap.add_argument("--fn", default="overlap", choices=["overlap", "gmm_l2", "bhattacharyya"],
@@ -812,6 +907,8 @@ def main():
         return run_ooc_workload(args)
     if args.workload == "cosine_sparse_n2500":
         return run_sparse_workload(args)
+    if args.workload == "pearson_list_n8192_d1048576":
+        return run_pearson_list_workload(args)
     if args.workload == "pearson_encoded_n2048_d1048576":
         return run_encoded_workload(args)
     if args.workload != "pearson_n8192_d1048576":

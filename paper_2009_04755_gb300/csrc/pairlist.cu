@@ -46,17 +46,31 @@ pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *_
     if (SPLIT) {
       // lane l takes column l of every 32-column block (64 contiguous bytes
       // per row and block for the warp)
+      // four blocks per trip, all sixteen loads issued before any product
+      // (Dp is a multiple of 64, so the block count is even, not always a
+      // multiple of four: the last trip may hold two)
       const int64_t nkb = Dp / kTcKBlock;
-      for (int64_t kb = 0; kb < nkb; ++kb) {
-        const int64_t col = kb * kTcKBlock + lane;
-        const size_t oa = blocked_offset(a, col, nkb, kTcKBlock);
-        const size_t ob = blocked_offset(b, col, nkb, kTcKBlock);
-        const float ha = __bfloat162float(hi[oa]), la = __bfloat162float(lo[oa]);
-        const float hb = __bfloat162float(hi[ob]), lb = __bfloat162float(lo[ob]);
-        part = fmaf(ha, hb, part);
-        part = fmaf(ha, lb, part);
-        part = fmaf(la, hb, part);
-        if ((kb & 63) == 63) {
+      constexpr size_t kBlock = (size_t)kRowBlock * kTcKBlock;   // elements per block
+      const size_t ra = blocked_offset(a, lane, nkb, kTcKBlock);
+      const size_t rb = blocked_offset(b, lane, nkb, kTcKBlock);
+      for (int64_t kb = 0; kb < nkb; kb += 4) {
+        float ha[4], la[4], hb[4], lb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool in = kb + u < nkb;
+          const size_t o = (size_t)(kb + u) * kBlock;
+          ha[u] = in ? __bfloat162float(hi[ra + o]) : 0.f;
+          la[u] = in ? __bfloat162float(lo[ra + o]) : 0.f;
+          hb[u] = in ? __bfloat162float(hi[rb + o]) : 0.f;
+          lb[u] = in ? __bfloat162float(lo[rb + o]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          part = fmaf(ha[u], hb[u], part);
+          part = fmaf(ha[u], lb[u], part);
+          part = fmaf(la[u], hb[u], part);
+        }
+        if ((kb & 63) == 60) {                     // 64 blocks per FP32 partial
           acc += (double)part;
           part = 0.f;
         }
