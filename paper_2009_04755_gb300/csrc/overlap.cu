@@ -391,7 +391,7 @@ overlap_kernel(Params P) {
 
     // fixed-order reduction over the chunks of each item, then the stores
     const int nI = c.i_end - c.i_begin;
-    for (int q = threadIdx.x; q < nI * nJ; q += kThreads) {
+    for (int q = threadIdx.x; q < nI * nJ; q += blockDim.x) {
       const int il = q / nJ, jl = q - il * nJ;
       if (diag && jl <= il) continue;
       const int i = c.i_begin + il, j = c.j_begin + jl;
@@ -565,15 +565,19 @@ cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s)
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // listed pairs are tiles of one item against one, a few row jobs each: one
+  // warp per CTA and many CTAs per SM keep the warps busy (20 ascent steps on
+  // 131K listed pairs: 114 ms at 8 warps per CTA, 89 at 4, 81 at 2, 79 at 1)
+  const int threads = cs.list_mode ? kThreads / 8 : kThreads;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > P.n_tiles) grid = P.n_tiles;
   e = cudaMemsetAsync(P.queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  kern<<<(int)grid, kThreads, smem, s>>>(P);
+  kern<<<(int)grid, threads, smem, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -190,6 +190,10 @@ ap_status cloud_list_plan(ap_items *it, const int32_t *pi, const int32_t *pj, in
   lc.n_tiles = n_pairs;
   lc.block_items = 1;
   lc.max_rj = max_row_jobs(single, cnt, 32LL * c.reg_r);
+  // a J block is one item: stage as many points as the largest item has
+  int64_t most = 4;
+  for (int64_t p = 0; p < c.n; ++p) most = std::max(most, c.h_poff[p + 1] - c.h_poff[p]);
+  lc.block_pts = (int32_t)std::min<int64_t>(most, c.block_pts);
   return AP_OK;
 }
 
