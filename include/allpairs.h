@@ -324,8 +324,11 @@ ap_status ap_ascent_list(ap_items *items, const int32_t *pi, const int32_t *pj, 
                          float *params, int32_t n_steps, float eta, float fmin, float *f_out,
                          int32_t *flags, void *stream);
 
-/* ap_destroy -- free everything the handle owns; NULL is accepted.  Waits for
- * the handle's outstanding work on its streams first. */
+/* ap_destroy -- free everything the handle owns (its device slots, pinned
+ * host cache, staging buffers, streams and plans: the storage levels of the
+ * cache hierarchy of Sec. IV-A, released when the item set is done); NULL is
+ * accepted.  Waits for the handle's outstanding work on its streams first.
+ * Errors: none (always AP_OK). */
 ap_status ap_destroy(ap_items *items);
 
 /* Statistics of the last ap_run_pairs (host struct, caller-owned). */
@@ -457,10 +460,10 @@ ap_status ap_plan_tiles(int64_t n, int32_t block, int32_t *out, int64_t cap,
 /*
  * ap_pearson_fp32_noalloc -- all-pairs Pearson correlation on the plain FP32
  * CUDA-core path, for callers that cannot let the library allocate GPU
- * memory (work recorded while a CUDA graph is being captured, processes whose
- * device memory is handed out by their own pool allocator, services with a
- * hard per-request memory limit).  The paper has no counterpart; this is an
- * addition of this library.
+ * memory: processes whose device memory is handed out by their own pool
+ * allocator (a cudaMalloc behind its back can fail or fragment the pool), and
+ * services with a hard per-request memory limit.  The paper has no
+ * counterpart; this is an addition of this library.
  *   data: device float[n_items][ld] (row-major, dim <= ld values per row,
  *         ld = 0 means ld = dim), caller-owned, read only;
  *   out:  device double[n_items(n_items-1)/2], packed as above, written.

@@ -7,9 +7,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -18,17 +20,21 @@
 
 namespace ap {
 
+// SM count of the current device, cached per device (first query under a lock)
 int num_sms() {
-  static int cached = -1;
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cached[kMaxDev];
+  static std::mutex mu;
   int dev = 0;
-  if (cached < 0) {
-    cudaGetDevice(&dev);
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
-      v = 1;
-    cached = v;
-  }
-  return cached;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  const bool fits = dev < kMaxDev;
+  int v = fits ? cached[dev].load(std::memory_order_acquire) : 0;
+  if (v > 0) return v;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+    v = 1;
+  if (fits) cached[dev].store(v, std::memory_order_release);
+  return v;
 }
 
 ap_status from_cuda(cudaError_t e) {

@@ -1,14 +1,13 @@
 // noalloc.cu -- all-pairs Pearson correlation on the plain FP32 CUDA-core
 // path without any device allocation by the library.
 //
-// Some callers cannot let a library allocate GPU memory: code that runs while
-// a CUDA graph is being captured (an allocation there is not allowed), hosts
-// whose GPU memory is carved up up front by a pool allocator that the library
-// must not bypass, or services with hard limits on what a request may
-// allocate.  This entry point takes the caller's raw vectors and output buffer
-// and keeps its own working memory (per-item means, inverse norms, the tile
-// queue counter and the status word) in one fixed, statically sized device
-// array, so it calls no cudaMalloc, cudaFree or allocating library routine.
+// Some callers cannot let a library allocate GPU memory: hosts whose GPU
+// memory is carved up up front by a pool allocator that the library must not
+// bypass, or services with hard limits on what a request may allocate.  This
+// entry point takes the caller's raw vectors and output buffer and keeps its
+// own working memory (per-item means, inverse norms and the tile-queue
+// counter) in one fixed, statically sized device array, so it calls no
+// cudaMalloc, cudaFree or allocating library routine.
 //
 // The array lives in this file as a `static __device__` object: every GPU
 // that loads the library holds AP_NOALLOC_SCRATCH_BYTES of it until the
@@ -24,11 +23,11 @@ namespace ap {
 namespace {
 
 constexpr int64_t kMaxItems = AP_NOALLOC_MAX_ITEMS;
-constexpr size_t kHeaderBytes = 256;                       // queue counter + status word
+constexpr size_t kHeaderBytes = 256;                       // queue counter, padded
 constexpr size_t kScratchBytes = kHeaderBytes + 2 * sizeof(double) * kMaxItems;
 static_assert(kScratchBytes == AP_NOALLOC_SCRATCH_BYTES, "scratch size out of sync");
 
-// [0]: int32 tile-queue head, [4]: int32 status word,
+// [0]: int32 tile-queue head (bytes 4..255 unused),
 // [256 ...): double mu[kMaxItems], double rs[kMaxItems]
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -138,7 +137,8 @@ noalloc_gram_f32_kernel(const float *__restrict__ X, int64_t n, int64_t D, int64
     int64_t I, J;
     tri_tile(t, nb, I, J);
     const int64_t i0 = I * 128, j0 = J * 128;
-    // loader: each thread stages 2 x 4 consecutive columns of one A row and one B row
+    // loader: per K block of 16, each thread stages 8 consecutive columns of
+    // one A row and one B row
     const int lrow = tid & 127, lq = tid >> 7;
     const int64_t ar = i0 + lrow, br = j0 + lrow;
     const bool a_ok = ar < n, b_ok = br < n;
@@ -224,8 +224,8 @@ extern "C" ap_status ap_pearson_fp32_noalloc(const float *data, int64_t n_items,
   int32_t *queue = reinterpret_cast<int32_t *>(base);
   double *mu = reinterpret_cast<double *>(base + kHeaderBytes);
   double *rs = mu + kMaxItems;
-  // the queue head (and status word) must start at zero on every call
-  e = cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+  // the queue head must start at zero on every call
+  e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return AP_ERR_CUDA;
   const int sgrid = (int)(n_items < 65535 ? n_items : 65535);
   noalloc_stats_kernel<<<sgrid, 512, 0, s>>>(data, n_items, dim, ld, mu, rs);

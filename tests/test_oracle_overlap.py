@@ -214,3 +214,85 @@ def test_ascent_step_increases_cost_near_alignment(oracle_lib):
         if f_prev is not None:
             assert np.all(f >= f_prev * (1 - 1e-12))
         f_prev = f
+
+
+def _single_point_pairs():
+    """Three pairs of single weighted points (item 2q against item 2q + 1)
+    whose Gaussian terms sit well below 1, so that a step scaled by grad f
+    instead of grad f / f moves the parameters by a visibly different
+    amount."""
+    xa = np.array([[0.10, -0.03], [-0.20, 0.15], [0.05, 0.05]])
+    xb = np.array([[0.02, 0.05], [-0.10, 0.02], [0.12, -0.04]])
+    sa = np.array([0.07, 0.06, 0.05])
+    sb = np.array([0.05, 0.08, 0.04])
+    wa = np.array([2.0, 0.7, 1.3])
+    wb = np.array([0.7, 1.9, 0.4])
+    pts = np.empty((6, 2))
+    pts[0::2], pts[1::2] = xa, xb
+    sig = np.empty(6); sig[0::2], sig[1::2] = sa, sb
+    w = np.empty(6); w[0::2], w[1::2] = wa, wb
+    c = {"dim": 2, "offsets": np.arange(7, dtype=np.int64),
+         "x": pts[:, 0].astype(np.float32), "y": pts[:, 1].astype(np.float32), "z": None,
+         "sigma": sig.astype(np.float32), "weight": w.astype(np.float32)}
+    params = np.array([[0.3, 0.01, -0.02], [-0.7, 0.05, 0.03], [1.1, -0.04, 0.06]])
+    return c, np.array([0, 2, 4]), np.array([1, 3, 5]), params
+
+
+def test_ascent_step_single_points_closed_form(oracle_lib):
+    # One point per item: f = wa wb e, e = exp(-|d|^2 / (2 s^2)),
+    # d = xa - (R(theta) xb + t), s^2 = sa^2 + sb^2.  Ascent on log f moves
+    # (theta, t) by eta grad f / f = eta (d . R'(theta) xb, d) / s^2: the
+    # weights and e cancel.  The values below are computed from the float32
+    # inputs with numpy, independently of the oracle.
+    c, pi, pj, p0 = _single_point_pairs()
+    eta = 1e-2
+    x = np.stack([c["x"], c["y"]], 1).astype(np.float64)
+    s = c["sigma"].astype(np.float64)
+    w = c["weight"].astype(np.float64)
+    want = p0.copy()
+    f_want = np.empty(3)
+    for q, (a, b) in enumerate(zip(pi, pj)):
+        th, t = p0[q, 0], p0[q, 1:]
+        R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        dR = np.array([[-np.sin(th), -np.cos(th)], [np.cos(th), -np.sin(th)]])
+        d = x[a] - (R @ x[b] + t)
+        s2 = s[a] ** 2 + s[b] ** 2
+        f_want[q] = w[a] * w[b] * np.exp(-(d @ d) / (2 * s2))
+        want[q, 0] += eta * (d @ (dR @ x[b])) / s2
+        want[q, 1:] += eta * d / s2
+    assert np.all((f_want > 0.05) & (f_want < 0.95 * w[pi] * w[pj]))   # e well below 1
+    got, f, g, flag = oracle_lib.ascent_step(c, pi, pj, p0, eta=eta)
+    assert not flag.any()
+    np.testing.assert_allclose(f, f_want, rtol=1e-13)
+    np.testing.assert_allclose(got - p0, want - p0, rtol=1e-11, atol=0)
+    # the step is eta grad f / f of the oracle's own (separately pinned) gradient
+    np.testing.assert_allclose(got - p0, eta * g / f[:, None], rtol=1e-13, atol=0)
+
+
+def test_ascent_step_skips_and_flags_below_fmin(oracle_lib):
+    # pairs whose f falls below fmin keep their parameters and are flagged;
+    # the others take their step as usual
+    c, pi, pj, p0 = _single_point_pairs()
+    f0, _ = oracle_lib.overlap_grad(c, pi, pj, p0)
+    fmin = float(np.median(f0))                 # pair with the smallest f is skipped
+    low = f0 < fmin
+    assert low.sum() == 1
+    got, f, g, flag = oracle_lib.ascent_step(c, pi, pj, p0, eta=1e-2, fmin=fmin)
+    assert np.array_equal(flag.astype(bool), low)
+    assert np.array_equal(got[low], p0[low])
+    assert np.all(np.abs(got[~low] - p0[~low]).max(1) > 0)
+    # every pair skipped when fmin exceeds all of them
+    got, _, _, flag = oracle_lib.ascent_step(c, pi, pj, p0, eta=1e-2, fmin=10.0)
+    assert flag.all() and np.array_equal(got, p0)
+
+
+def test_ascent_step_goes_uphill_on_log_f(oracle_lib):
+    # a small step must raise log f by about eta |grad log f|^2 (first order):
+    # a sign error lowers f, a missing 1/f scales the gain by f
+    c, pi, pj, p0 = _single_point_pairs()
+    eta = 1e-6
+    got, f, g, _ = oracle_lib.ascent_step(c, pi, pj, p0, eta=eta)
+    f1, _ = oracle_lib.overlap_grad(c, pi, pj, got)
+    gain = np.log(f1) - np.log(f)
+    first_order = eta * ((g / f[:, None]) ** 2).sum(1)
+    np.testing.assert_allclose(gain, first_order, rtol=1e-3)

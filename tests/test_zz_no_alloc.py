@@ -1,10 +1,11 @@
 """The allocation-free Pearson entry point (ap_pearson_fp32_noalloc).
 
 It serves callers that must not let the library allocate GPU memory, for
-example work recorded inside CUDA graph capture or processes whose device
-memory is owned by their own pool allocator.  Checked here through the C ABI
-against the library's regular FP32 path, on two calls in a row, plus its
-size limit and that a call leaves the device's free memory unchanged.
+example processes whose device memory is owned by their own pool allocator,
+or services with a hard cap on what one request may allocate.  Checked here
+through the C ABI against the FP64 oracle element by element and against the
+library's regular FP32 path, on two calls in a row, plus its size limit and
+that a call leaves the device's free memory unchanged.
 """
 import ctypes
 
@@ -41,23 +42,28 @@ def _regular(ap, X):
         return it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32).cpu().numpy()
 
 
-def test_noalloc_matches_regular_fp32_path_twice(lib):
+def test_noalloc_matches_oracle_and_regular_fp32_path_twice(lib, oracle_lib):
     ap, fn = lib
     n, D = 300, 1500
     pi, pj = np.triu_indices(n, 1)
     for seed in (21, 22):                       # two calls in a row, different data
-        X = synth.vectors_grouped(n, D, seed=seed).cuda()
+        Xh = synth.vectors_grouped(n, D, seed=seed)
+        X = Xh.cuda()
         out = torch.full((n * (n - 1) // 2,), float("nan"), dtype=torch.float64, device="cuda")
         assert _noalloc(fn, X, out) == ap.binding.AP_OK
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        want = _regular(ap, X)
-        tol = pearson_tolerance(X.cpu().numpy(), pi, pj, ap.AP_PREC_FP32)
+        tol = pearson_tolerance(Xh.numpy(), pi, pj, ap.AP_PREC_FP32)
         assert np.all(np.isfinite(got))
+        # the FP64 oracle on every pair, element by element
+        ref = oracle_lib.pearson(Xh.numpy(), pi, pj)
+        assert np.all(np.abs(got - ref) <= tol), float(np.abs(got - ref).max())
+        # and the library's regular FP32 path on the same rows
+        want = _regular(ap, X)
         assert np.all(np.abs(got - want) <= tol), float(np.abs(got - want).max())
 
 
-def test_noalloc_ragged_rows_and_stride(lib):
+def test_noalloc_ragged_rows_and_stride(lib, oracle_lib):
     ap, fn = lib
     n, D, ld = 131, 77, 80                      # ragged tiles, unaligned row stride
     base = torch.randn(n, ld, device="cuda")
@@ -69,6 +75,8 @@ def test_noalloc_ragged_rows_and_stride(lib):
     pi, pj = np.triu_indices(n, 1)
     tol = pearson_tolerance(X.cpu().numpy(), pi, pj, ap.AP_PREC_FP32)
     assert np.all(np.abs(out.cpu().numpy() - want) <= tol)
+    ref = oracle_lib.pearson(X.cpu().numpy(), pi, pj)
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= tol)
 
 
 def test_noalloc_allocates_nothing_and_rejects_oversize(lib):
