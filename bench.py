@@ -33,7 +33,7 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 # 8192 x 2^20 with its default schedule (64 column ranges per tile), captured
 # at full size (a one-pass metric set) on the kernel as it stands; None
 # whenever the kernel has changed since the capture
-GRAM_TRAFFIC_BYTES = 305428372992 + 17525829632
+GRAM_TRAFFIC_BYTES = {"gram_tc_kernel": 305428372992 + 17525829632}
 
 
 def peaks():
@@ -214,9 +214,11 @@ def ours(args):
     stream = torch.cuda.current_stream()
     X = synth.vectors_grouped(n, D, seed=0, device="cuda")
     items = ap.Items.from_vectors(X, precisions=(ap.AP_PREC_SPLIT_BF16,))
-    if args.k_split >= 0:
-        items.set_plan(128, 256, 0, args.k_split)
-    k_split = items.plan()["k_split"]
+    if args.k_split >= 0 or args.mma_ctas:
+        items.set_plan(128, 256, 0, args.k_split, args.mma_ctas)
+    plan = items.plan()
+    k_split, mma_ctas = plan["k_split"], plan["mma_ctas"]
+    gram_kernel = "gram_tc2_kernel" if mma_ctas == 2 else "gram_tc_kernel"
     out = torch.empty(P, dtype=torch.float64, device="cuda")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 2)]
 
@@ -254,10 +256,11 @@ def ours(args):
     flops_launch = 3 * 2.0 * D * P          # three BF16 products per pair, 2 flops per MAC
     achieved_tf = flops_launch / (gram_avg / 1e3) / 1e12
     # the capture covers the default 8192 x 2^20 schedule only
-    traffic = GRAM_TRAFFIC_BYTES if (n, D, k_split) == (N_ITEMS, DIM, 64) else None
+    traffic = (GRAM_TRAFFIC_BYTES.get(gram_kernel)
+               if (n, D, k_split) == (N_ITEMS, DIM, 64) else None)
     roofline = {"bound": "tensor", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic,
-                "kernel": "gram_tc_kernel", "peak_kind": f"{pk_kind} bf16 sustained",
+                "kernel": gram_kernel, "peak_kind": f"{pk_kind} bf16 sustained",
                 "algorithmic_flops_per_launch": flops_launch}
 
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
@@ -266,6 +269,7 @@ def ours(args):
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
             "config": {"workload": f"pearson_n{n}_d{D}", "n_items": n, "dim": D,
                        "pairs": P, "precision": "split-bf16", "k_split": k_split,
+                       "mma_ctas": mma_ctas,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (32 GiB raw + 32 GiB hi/lo) far larger than L2"},
             "roofline": roofline, "gram_ms": gram_avg,
@@ -892,6 +896,9 @@ def main():
     ap.add_argument("--k-split", type=int, default=-1,
                     help="Pearson Gram schedule: column ranges per tile (0 whole tiles; "
                          "-1 the library default)")
+    ap.add_argument("--mma-ctas", type=int, default=0, choices=[0, 1, 2],
+                    help="Pearson Gram: CTAs per tensor-core MMA (1 one CTA per tile, 2 CTA "
+                         "pairs; 0 the library default)")
     ap.add_argument("--ooc-policy", type=int, default=2, choices=[0, 1, 2],
                     help="out-of-core schedule: 0 resident+streamed, 1 recursive order + LRU, "
                          "2 column slices")

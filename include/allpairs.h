@@ -185,7 +185,13 @@ typedef struct ap_plan {
    * 16384 columns and at least two units per SM, at most one range per 64
    * columns; 0 where that gives one range */
   int32_t k_split;
-  int32_t reserved;
+  /* vector sets only: CTAs per tensor-core MMA.  2 (the default; 0 in
+   * ap_set_plan asks for it): the units are 256 x 256 block pairs, each
+   * computed by a cluster of two CTAs on neighbouring SMs with one
+   * tcgen05.mma.cta_group::2 (each CTA stages its own 128 rows and half of
+   * the other block); 1: one CTA per 128 x 256 tile.  Results agree to
+   * rounding (the same products, chained the same way). */
+  int32_t mma_ctas;
 } ap_plan;
 
 /*
@@ -424,7 +430,11 @@ typedef enum {
    * so the consumer's wait runs out: the kernel records a device error code
    * (read with ap_last_device_error), every role leaves, TMEM is freed and
    * the context stays usable */
-  AP_DEBUG_WITHHOLD_STAGE = 1
+  AP_DEBUG_WITHHOLD_STAGE = 1,
+  /* as above, but the withheld stage is the sixth of each tile (its last when
+   * it has fewer), so the wait runs out with tensor-core MMAs of the tile
+   * already issued: they are drained before TMEM is freed */
+  AP_DEBUG_WITHHOLD_LATER_STAGE = 2
 } ap_debug_flags;
 
 /* ap_set_debug -- set the failure-path switch and the wall-clock budget of
@@ -434,6 +444,11 @@ ap_status ap_set_debug(ap_items *items, int32_t flags, uint64_t wait_budget_ns);
 
 /* Static, NUL-terminated description of a status code. */
 const char *ap_status_string(ap_status s);
+
+/* Name of the CUDA error behind the calling thread's most recent AP_ERR_CUDA
+ * or AP_ERR_OOM return (e.g. "cudaErrorInvalidValue"); "" if there was none.
+ * Static string; diagnostic only. */
+const char *ap_last_cuda_error(void);
 
 /* Code recorded by a bounded device wait that ran out during the handle's
  * last synchronised call (0 = none); also cleared by this call. */
@@ -456,6 +471,22 @@ int64_t ap_pair_index(int64_t i, int64_t j, int64_t n);
  */
 ap_status ap_plan_tiles(int64_t n, int32_t block, int32_t *out, int64_t cap,
                         int64_t *n_tiles);
+
+/*
+ * ap_pipe_rate -- measured issue rate of one SM pipe on the current device,
+ * the denominator of the CUDA-core kernels' rooflines (measurement support;
+ * the paper reports no kernel-level rates and has no counterpart).
+ *   pipe 0: FP32 fused multiply-add (FMA results; 2 flops each),
+ *   pipe 1: MUFU ex2.approx results, pipe 2: MUFU rcp.approx results.
+ * Every SM runs 64 warps of eight independent chains of the instruction for a
+ * few milliseconds (synchronous, legacy default stream; one small temporary
+ * device allocation).  Writes results per clock per SM (from the SMs' cycle
+ * counters), results per second over the whole GPU (CUDA events) and, if
+ * sm_mhz is not NULL, the SM clock seen during the run.  Changes no GPU
+ * setting.  Errors: AP_ERR_INVALID_ARG (unknown pipe, NULL outputs),
+ * AP_ERR_CUDA / AP_ERR_OOM.
+ */
+ap_status ap_pipe_rate(int32_t pipe, double *per_clk_per_sm, double *per_s, double *sm_mhz);
 
 /*
  * ap_pearson_fp32_noalloc -- all-pairs Pearson correlation on the plain FP32

@@ -51,7 +51,7 @@ class RunStats(ctypes.Structure):
 class Plan(ctypes.Structure):
     _fields_ = [("block_items", ctypes.c_int32), ("block_pts", ctypes.c_int32),
                 ("reg_r", ctypes.c_int32), ("sorted", ctypes.c_int32), ("rate", ctypes.c_double),
-                ("k_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("k_split", ctypes.c_int32), ("mma_ctas", ctypes.c_int32)]
 
 
 class APError(RuntimeError):
@@ -82,6 +82,7 @@ def lib():
             "ap_destroy": (i32, [vp]),
             "ap_get_stats": (i32, [vp, ctypes.POINTER(RunStats)]),
             "ap_status_string": (ctypes.c_char_p, [i32]),
+            "ap_last_cuda_error": (ctypes.c_char_p, []),
             "ap_last_device_error": (i32, [vp]),
             "ap_pair_count": (i64, [i64]),
             "ap_pair_index": (i64, [i64, i64, i64]),
@@ -97,6 +98,9 @@ def lib():
             "ap_run_pairs_list": (i32, [vp, i32, i32, vp, vp, i64, vp, vp, vp]),
             "ap_backward_list": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
             "ap_ascent_list": (i32, [vp, vp, vp, i64, vp, i32, f32, f32, vp, vp, vp]),
+            "ap_pipe_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -119,6 +123,10 @@ def status_string(s: int) -> str:
 
 def check(status: int, what: str):
     if status != AP_OK:
+        if status in (AP_ERR_OOM, AP_ERR_CUDA):
+            cuda = lib().ap_last_cuda_error().decode()
+            if cuda:
+                what = f"{what} [{cuda}]"
         raise APError(status, what)
 
 
@@ -128,6 +136,19 @@ def pair_count(n: int) -> int:
 
 def pair_index(i: int, j: int, n: int) -> int:
     return int(lib().ap_pair_index(int(i), int(j), int(n)))
+
+
+PIPE_FMA, PIPE_EX2, PIPE_RCP = 0, 1, 2
+
+
+def pipe_rate(pipe: int) -> dict:
+    """Measured issue rate of one SM pipe on the current device
+    (ap_pipe_rate): results per clock per SM, per second, and the SM clock
+    seen during the probe."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib().ap_pipe_rate(int(pipe), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "ap_pipe_rate")
+    return {"per_clk_per_sm": a.value, "per_s": b.value, "sm_mhz": c.value}
 
 
 def plan_tiles(n: int, block: int):
@@ -423,10 +444,13 @@ class Items:
         check(lib().ap_get_plan(self._h, ctypes.byref(p)), "ap_get_plan")
         return {k: getattr(p, k) for k, _ in Plan._fields_}
 
-    def set_plan(self, block_items: int, block_pts: int, reg_r: int = 0, k_split: int = 0):
+    def set_plan(self, block_items: int, block_pts: int, reg_r: int = 0, k_split: int = 0,
+                 mma_ctas: int = 0):
         """Clouds: tile plan (block_items, block_pts, reg_r).  Vector sets:
-        (128, 256) and k_split, the schedule of the split-BF16 Gram."""
-        p = Plan(int(block_items), int(block_pts), int(reg_r), 0, 0.0, int(k_split), 0)
+        (128, 256), k_split (the split-BF16 Gram's column ranges) and
+        mma_ctas (1: one CTA per tile, 2 or 0: CTA pairs)."""
+        p = Plan(int(block_items), int(block_pts), int(reg_r), 0, 0.0, int(k_split),
+                 int(mma_ctas))
         check(lib().ap_set_plan(self._h, ctypes.byref(p)), "ap_set_plan")
 
     def stats(self) -> dict:

@@ -26,6 +26,7 @@ enum DeviceError : int32_t {
   DEV_TIMEOUT_ACCUM = 3,    // epilogue gave up waiting for the accumulator
   DEV_TIMEOUT_STAGE = 4,    // a bulk copy of item data did not land
   DEV_TIMEOUT_SLOT = 5,     // a slot-ready flag was never raised
+  DEV_TIMEOUT_UNIT = 6,     // a CTA pair's unit hand-out ring did not advance
 };
 
 // wall-clock budget of one device wait (nanoseconds, %globaltimer)
@@ -173,6 +174,12 @@ struct VecStore {
   // k_split > 0: the tiles run as split-K units in waves (panel_units)
   int32_t k_split = 0;
   int32_t *d_panel_units = nullptr; int64_t n_panel_units = 0;
+  // mma_ctas = 2: the same schedule on CTA pairs (gram_tc2.cu): split-K units
+  // in waves of tc2_pairs() macro pairs, and one unit per macro pair (whole
+  // columns: k_split = 0 and coverage)
+  int32_t mma_ctas = 2;
+  int32_t *d_pair_units = nullptr; int64_t n_pair_units = 0;
+  int32_t *d_pair_whole = nullptr; int64_t n_pair_whole = 0;
   std::vector<int32_t> h_tiles_tc;
   int32_t *d_tiles_f32 = nullptr; int64_t n_tiles_f32 = 0;
   void *tmap_hi = nullptr, *tmap_lo = nullptr;   // CUtensorMap (host copies)
@@ -321,6 +328,23 @@ cudaError_t launch_gram_tc(const void *tmap_hi, const void *tmap_lo, int64_t n, 
                            int32_t *queue, int32_t *status, double *g64, void *out,
                            int coverage, int ooc, uint64_t budget, int32_t debug,
                            cudaStream_t s);
+// split-BF16 Gram on CTA pairs (gram_tc2.cu): units of kOocTileInts int32
+// {A row block of CTA 0, of CTA 1, B row block of CTA 0, of CTA 1, first row
+// block (128 items) of the I block, J block (256 items), first chunk, end
+// chunk}; atomic = 1 adds partial Grams into FP64 out, 0 writes G rs_i rs_j
+// of whole block pairs, coverage = 1 counts pairs into int32 out.
+cudaError_t launch_gram_tc2(const void *tmap_hi, const void *tmap_lo, int64_t n, const double *rs,
+                            const int32_t *units, int64_t n_units, int32_t *queue,
+                            int32_t *status, double *g64, void *out, int coverage, int atomic,
+                            uint64_t budget, int32_t debug, cudaStream_t s);
+// CTA pairs of one launch (clusters of two that fit on the device at once)
+int64_t tc2_pairs();
+// units of the CTA-pair Gram over the resident set: macro pairs (I <= J, 256
+// items each) in recursive quadrant order, in waves of `group` macro pairs,
+// k_split column ranges of the nchunks 64-column chunks per wave (k_split <= 1:
+// one unit per macro pair over all columns)
+void pair_units(int64_t n, int64_t nchunks, int64_t group, int64_t k_split,
+                std::vector<int32_t> &units);
 // out-of-core unit: {A row block, B row blocks (2), I block, J block, chunk
 // begin, chunk end, unused}; chunks are 64 columns of D
 constexpr int kOocTileInts = 8;
@@ -347,7 +371,7 @@ void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t gro
 // the split-K schedule of a vector set's split-BF16 Gram: k_split column
 // ranges per tile (0 whole tiles, -1 the default rule of default_k_split)
 int32_t default_k_split(int64_t n_tiles, int64_t Dp);
-ap_status set_vector_plan(ap_items *it, int32_t k_split);
+ap_status set_vector_plan(ap_items *it, int32_t k_split, int32_t mma_ctas = 0);
 
 // the particle scores' re-scaled cloud storage and L2 self terms, built on
 // first use (api.cu)

@@ -37,8 +37,12 @@ int num_sms() {
   return v;
 }
 
+// the CUDA error behind this thread's last AP_ERR_CUDA / AP_ERR_OOM
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 ap_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return AP_OK;
+  g_last_cuda_error = e;
   cudaGetLastError();   // clear a non-sticky error so later calls can run
   return e == cudaErrorMemoryAllocation ? AP_ERR_OOM : AP_ERR_CUDA;
 }
@@ -59,7 +63,7 @@ void free_items(ap_items *it) {
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
   dfree(v.d_partc); dfree(v.d_delta_all); dfree(v.d_recentre);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
-  dfree(v.d_panel_units);
+  dfree(v.d_panel_units); dfree(v.d_pair_units); dfree(v.d_pair_whole);
   free_out_of_core(v);
   free_sparse(it->sp);
   free_tc_tensor_maps(v.tmap_hi, v.tmap_lo);
@@ -363,6 +367,10 @@ int64_t ap_pair_index(int64_t i, int64_t j, int64_t n) {
   return pair_index(i, j, n);
 }
 
+const char *ap_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "" : cudaGetErrorName(g_last_cuda_error);
+}
+
 const char *ap_status_string(ap_status s) {
   switch (s) {
     case AP_OK: return "ok";
@@ -476,16 +484,33 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
     if (cover) use_split = have_split;
     if (use_split && !have_split) return AP_ERR_STATE;
     if (!use_split && !have_f32) return AP_ERR_STATE;
+    const bool pairs = v.mma_ctas == 2;
     if (use_split && !cover && v.k_split > 0) {
       // split-K units in waves: partial Grams meet in FP64 in `out`
       AP_TRY(cudaMemsetAsync(out, 0, (size_t)(n * (n - 1) / 2) * sizeof(double), s));
-      AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_panel_units,
-                            v.n_panel_units, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
-                            it->wait_budget_ns, it->debug, s));
+      if (pairs)
+        AP_TRY(launch_gram_tc2(v.tmap_hi, v.tmap_lo, v.n, v.d_rs, v.d_pair_units, v.n_pair_units,
+                               it->d_queue, it->d_status, v.d_g64, out, 0, 1,
+                               it->wait_budget_ns, it->debug, s));
+      else
+        AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_panel_units,
+                              v.n_panel_units, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
+                              it->wait_budget_ns, it->debug, s));
       AP_TRY(launch_pair_finalize(reinterpret_cast<double *>(out), v.d_rs, v.d_delta_all, v.n,
                                   v.D, s));
-      it->stats.tiles = v.n_panel_units;
-      it->stats.tile_m = kTcTileM;
+      it->stats.tiles = pairs ? v.n_pair_units : v.n_panel_units;
+      it->stats.tile_m = pairs ? 2 * kTcTileM : kTcTileM;
+      it->stats.tile_n = kTcTileN;
+    } else if (use_split && pairs) {
+      // whole block pairs (or coverage) on CTA pairs
+      AP_TRY(launch_gram_tc2(v.tmap_hi, v.tmap_lo, v.n, v.d_rs, v.d_pair_whole, v.n_pair_whole,
+                             it->d_queue, it->d_status, v.d_g64, out, cover, 0,
+                             it->wait_budget_ns, it->debug, s));
+      if (!cover)
+        AP_TRY(launch_pair_correct(reinterpret_cast<double *>(out), v.d_rs, v.d_delta_all, v.n,
+                                   v.D, s));
+      it->stats.tiles = v.n_pair_whole;
+      it->stats.tile_m = 2 * kTcTileM;
       it->stats.tile_n = kTcTileN;
     } else if (use_split) {
       AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs, v.d_tiles_tc, v.n_tiles_tc,
@@ -588,7 +613,9 @@ ap_status ap_get_stats(const ap_items *it, ap_run_stats *out) {
 
 ap_status ap_set_debug(ap_items *it, int32_t flags, uint64_t wait_budget_ns) {
   if (!it) return AP_ERR_INVALID_ARG;
-  if (flags != AP_DEBUG_NONE && flags != AP_DEBUG_WITHHOLD_STAGE) return AP_ERR_INVALID_ARG;
+  if (flags != AP_DEBUG_NONE && flags != AP_DEBUG_WITHHOLD_STAGE &&
+      flags != AP_DEBUG_WITHHOLD_LATER_STAGE)
+    return AP_ERR_INVALID_ARG;
   it->debug = flags;
   it->wait_budget_ns = wait_budget_ns;
   return AP_OK;

@@ -18,18 +18,21 @@
 //               register sums (FP64 every 16384 columns), then FP64 scaling
 //               and packed upper-triangle stores once per tile.
 // Every wait is bounded (a per-launch budget, 2 s by default); when one runs
-// out the CTA records a device error code, drains its in-flight copies, frees
-// TMEM and returns.
+// out the CTA records a device error code, drains its in-flight copies and
+// the MMAs it has issued, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "ap_internal.h"
+#include "tc_ptx.cuh"
 
 namespace ap {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = kTcTileM;                 // 128 rows of the I block
 constexpr int BN = kTcTileN;                 // 256 rows of the J block
@@ -54,73 +57,6 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barrier
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait: false when the budget ran out or another role aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          volatile int *abort_flag, uint64_t budget) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (*abort_flag) return false;
-      if (global_ns() - t0 > budget) return false;
-    }
-  }
-}
-
-// one 128-row x 32-column block of the blocked copy: coordinates
-// {column in block, row in block, column block, row block}
-__device__ __forceinline__ void tma_load_block(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                               int32_t kb, int32_t rb) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %3, %4, %5}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(0), "r"(kb), "r"(rb)
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major operand, 64-byte swizzle,
-// 8-row core-matrix groups 512 bytes apart
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused, K fits the atom)
-  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)4 << 61;                    // swizzle mode: 64 B
-  return d;
-}
-
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                           uint32_t accumulate) {
   asm volatile(
@@ -137,35 +73,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-
-
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-      "r"(v[15])
-      : "memory");
-}
 // Chains of a unit's nkb k-blocks: two head chains of kHeadStages, then
 // chains of kChainStages; the last one may be shorter.
 __device__ __forceinline__ int64_t chain_first(int64_t c) {
@@ -206,8 +113,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
   volatile int *s_abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
   int *s_tile = reinterpret_cast<int *>(tmem_slot + 2);
 
@@ -217,6 +124,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
   auto empty_bar = [&](int s) { return smem_u32(&bars[STAGES + s]); };
   auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * STAGES + a]); };
   auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * STAGES + 2 + a]); };
+  const uint32_t drain_bar = smem_u32(&bars[2 * STAGES + 4]);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -227,6 +135,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
       mbar_init(tfull_bar(a), 1);
       mbar_init(tempty_bar(a), kEpiWarps);
     }
+    mbar_init(drain_bar, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -289,9 +198,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
         }
         const uint32_t fb = full_bar(p_stage);
         const uint32_t sb = smem_base + p_stage * STAGE_BYTES;
-        // debug 1 withholds the first stage of every tile: the consumer's
-        // bounded wait must run out and report (failure-path testing only)
-        if (debug == 1 && kb == kb0) {
+        // debug 1 withholds the first stage of every tile, debug 2 its sixth
+        // (or last) stage, after MMAs of the tile have been issued: the
+        // consumer's bounded wait must run out and report (failure-path
+        // testing only)
+        if ((debug == 1 && kb == kb0) ||
+            (debug == 2 && kb == kb0 + (nkb > 5 ? 5 : nkb - 1))) {
           if (++p_stage == STAGES) { p_stage = 0; p_phase ^= 1; }
           continue;
         }
@@ -459,6 +371,20 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant_
   }
   __syncthreads();
   if (warp == 1) {
+    // every MMA this thread issued must have landed before its accumulators
+    // are freed: after an abort mid-chain some were never committed to an
+    // accumulator barrier, so commit them all to one of their own and wait
+    if (lane == 0) {
+      umma_commit(drain_bar);
+      const uint64_t t0 = global_ns();
+      while (!mbar_try_wait(drain_bar, 0)) {
+        if (global_ns() - t0 > budget) {
+          atomicCAS(status, 0, DEV_TIMEOUT_ACCUM);
+          break;
+        }
+      }
+    }
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS)

@@ -120,4 +120,28 @@ void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t gro
   }
 }
 
+void pair_units(int64_t n, int64_t nchunks, int64_t group, int64_t k_split,
+                std::vector<int32_t> &units) {
+  // macro pairs of 256 items; each CTA of a pair takes one 128-item half of
+  // the I macro and stages one half of the J macro
+  units.clear();
+  std::vector<int32_t> macro;
+  dc_block_pairs((n + kTcTileN - 1) / kTcTileN, macro);
+  const int64_t nt = (int64_t)macro.size() / 2;
+  k_split = std::max<int64_t>(1, std::min<int64_t>(k_split, nchunks));
+  group = std::max<int64_t>(1, group);
+  for (int64_t w0 = 0; w0 < nt; w0 += group) {
+    const int64_t w1 = std::min<int64_t>(nt, w0 + group);
+    for (int64_t p = 0; p < k_split; ++p) {
+      const int32_t c0 = (int32_t)(p * nchunks / k_split);
+      const int32_t c1 = (int32_t)((p + 1) * nchunks / k_split);
+      for (int64_t t = w0; t < w1; ++t) {
+        const int32_t I = macro[2 * t], J = macro[2 * t + 1];
+        const int32_t u[kOocTileInts] = {2 * I, 2 * I + 1, 2 * J, 2 * J + 1, 2 * I, J, c0, c1};
+        units.insert(units.end(), u, u + kOocTileInts);
+      }
+    }
+  }
+}
+
 }  // namespace ap

@@ -101,7 +101,7 @@ using namespace ap;
 extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
   if (!it || !out) return AP_ERR_INVALID_ARG;
   out->k_split = 0;
-  out->reserved = 0;
+  out->mma_ctas = 0;
   if (it->kind == AP_ITEMS_SPARSE) {
     out->block_items = out->block_pts = kSparseBlock;
     out->reg_r = out->sorted = 0;
@@ -115,6 +115,7 @@ extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
     out->sorted = 0;
     out->rate = 0.0;
     out->k_split = it->vec.k_split;
+    out->mma_ctas = it->vec.mma_ctas;
     return AP_OK;
   }
   out->block_items = it->cl.block_items;
@@ -134,25 +135,49 @@ int32_t ap::default_k_split(int64_t n_tiles, int64_t Dp) {
   return k <= 1 ? 0 : (int32_t)k;
 }
 
-// vector sets: (re)build the split-K wave units of the tensor-core tiles
-ap_status ap::set_vector_plan(ap_items *it, int32_t k_split) {
+namespace {
+ap_status upload_units(const std::vector<int32_t> &units, int32_t **d, int64_t *n) {
+  dfree(*d);
+  *n = 0;
+  AP_TRY(dmalloc(d, std::max<size_t>(units.size(), kOocTileInts)));
+  if (!units.empty())
+    AP_TRY(cudaMemcpy(*d, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
+  *n = (int64_t)units.size() / kOocTileInts;
+  return AP_OK;
+}
+}  // namespace
+
+// vector sets: (re)build the split-K wave units of the tensor-core tiles,
+// for one CTA per tile (mma_ctas 1) or CTA pairs (mma_ctas 2; 0 = 2)
+ap_status ap::set_vector_plan(ap_items *it, int32_t k_split, int32_t mma_ctas) {
   VecStore &v = it->vec;
   if (v.out_of_core) return AP_ERR_STATE;
   if (!v.d_hi) return AP_ERR_STATE;
+  if (mma_ctas == 0) mma_ctas = 2;
+  if (mma_ctas != 1 && mma_ctas != 2) return AP_ERR_INVALID_ARG;
   if (k_split < 0) k_split = default_k_split(v.n_tiles_tc, v.Dp);
   cudaError_t e = cudaDeviceSynchronize();      // the old units may still be in use
   if (e != cudaSuccess) return from_cuda(e);
   dfree(v.d_panel_units);
-  v.n_panel_units = 0;
+  dfree(v.d_pair_units);
+  dfree(v.d_pair_whole);
+  v.n_panel_units = v.n_pair_units = v.n_pair_whole = 0;
   v.k_split = 0;
-  if (k_split == 0) return AP_OK;
+  v.mma_ctas = mma_ctas;
+  const int64_t nch = v.Dp / kOocChunkCols;
   std::vector<int32_t> units;
-  panel_units(v.h_tiles_tc, v.Dp / kOocChunkCols, tc_grid(v.n_tiles_tc), k_split, units);
-  const int64_t nu = (int64_t)units.size() / kOocTileInts;
-  AP_TRY(dmalloc(&v.d_panel_units, std::max<size_t>(units.size(), kOocTileInts)));
-  if (!units.empty())
-    AP_TRY(cudaMemcpy(v.d_panel_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
-  v.n_panel_units = nu;
+  if (mma_ctas == 2) {
+    pair_units(v.n, nch, tc2_pairs(), 1, units);          // whole columns, one per macro pair
+    AP_TRY_ST(upload_units(units, &v.d_pair_whole, &v.n_pair_whole));
+  }
+  if (k_split == 0) return AP_OK;
+  if (mma_ctas == 2) {
+    pair_units(v.n, nch, tc2_pairs(), k_split, units);
+    AP_TRY_ST(upload_units(units, &v.d_pair_units, &v.n_pair_units));
+  } else {
+    panel_units(v.h_tiles_tc, nch, tc_grid(v.n_tiles_tc), k_split, units);
+    AP_TRY_ST(upload_units(units, &v.d_panel_units, &v.n_panel_units));
+  }
   v.k_split = k_split;
   return AP_OK;
 }
@@ -163,7 +188,8 @@ extern "C" ap_status ap_set_plan(ap_items *it, const ap_plan *plan) {
   if (it->kind == AP_ITEMS_VECTOR) {
     if (plan->block_items != kTcTileM || plan->block_pts != kTcTileN) return AP_ERR_INVALID_ARG;
     if (plan->k_split < -1 || plan->k_split > kMaxKSplit) return AP_ERR_INVALID_ARG;
-    return set_vector_plan(it, plan->k_split);
+    if (plan->mma_ctas < 0 || plan->mma_ctas > 2) return AP_ERR_INVALID_ARG;
+    return set_vector_plan(it, plan->k_split, plan->mma_ctas);
   }
   if (plan->block_items < 1 || plan->block_items > kOverlapMaxBlockItems) return AP_ERR_INVALID_ARG;
   if (plan->block_pts < 64 || plan->block_pts > 8192) return AP_ERR_INVALID_ARG;
