@@ -477,7 +477,9 @@ ap_status ap_plan_tiles(int64_t n, int32_t block, int32_t *out, int64_t cap,
  * the denominator of the CUDA-core kernels' rooflines (measurement support;
  * the paper reports no kernel-level rates and has no counterpart).
  *   pipe 0: FP32 fused multiply-add (FMA results; 2 flops each),
- *   pipe 1: MUFU ex2.approx results, pipe 2: MUFU rcp.approx results.
+ *   pipe 1: MUFU ex2.approx results, pipe 2: MUFU rcp.approx results,
+ *   pipe 3: packed FP32x2 fused multiply-add (FMA results, two per
+ *           instruction).
  * Every SM runs 64 warps of eight independent chains of the instruction for a
  * few milliseconds (synchronous, legacy default stream; one small temporary
  * device allocation).  Writes results per clock per SM (from the SMs' cycle

@@ -138,7 +138,7 @@ def pair_index(i: int, j: int, n: int) -> int:
     return int(lib().ap_pair_index(int(i), int(j), int(n)))
 
 
-PIPE_FMA, PIPE_EX2, PIPE_RCP = 0, 1, 2
+PIPE_FMA, PIPE_EX2, PIPE_RCP, PIPE_FMA2 = 0, 1, 2, 3
 
 
 def pipe_rate(pipe: int) -> dict:

@@ -40,25 +40,41 @@ __device__ __forceinline__ float op_rcp(float x) {
 }
 
 // PIPE 0: fmaf chains; 1: ex2 chains (x -> 2^-x stays in [0.5, 1]);
-// 2: rcp chains (x -> 1/x alternates between two values)
+// 2: rcp chains x -> 1 / (x + c) (the add keeps two reciprocals in a row from
+// cancelling; it runs on the FMA pipe, eight times wider than the MUFU's
+// reciprocal); 3: packed FP32x2 fma chains (two results per instruction,
+// counted as two)
 template <int PIPE>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
 pipe_probe_kernel(int iters, float *sink, unsigned long long *cycles, unsigned long long *ns) {
   float a[kChains];
+  float2 a2[kChains / 2];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = 0.5f + 1e-4f * (float)(threadIdx.x + 37 * k);
+#pragma unroll
+  for (int k = 0; k < kChains / 2; ++k) a2[k] = make_float2(a[2 * k], a[2 * k + 1]);
   const float m = 0.9999f, c = 1e-4f;
+  const float2 m2 = make_float2(m, m), c2 = make_float2(c, c);
   __syncthreads();
   const unsigned long long c0 = clock64();
   const uint64_t t0 = gtimer();
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
+      if (PIPE == 3) {
+        // twice the chains of one packed instruction each: the same results
+        // per thread as the scalar probe
 #pragma unroll
-      for (int k = 0; k < kChains; ++k) {
-        if (PIPE == 0) a[k] = fmaf(a[k], m, c);
-        else if (PIPE == 1) a[k] = op_ex2(a[k]);
-        else a[k] = op_rcp(a[k]);
+        for (int k = 0; k < kChains / 2; ++k) a2[k] = __ffma2_rn(a2[k], m2, c2);
+#pragma unroll
+        for (int k = 0; k < kChains / 2; ++k) a2[k] = __ffma2_rn(a2[k], m2, c2);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) {
+          if (PIPE == 0) a[k] = fmaf(a[k], m, c);
+          else if (PIPE == 1) a[k] = op_ex2(a[k]);
+          else a[k] = op_rcp(a[k] + c);
+        }
       }
     }
   }
@@ -68,6 +84,8 @@ pipe_probe_kernel(int iters, float *sink, unsigned long long *cycles, unsigned l
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kChains; ++k) s += a[k];
+#pragma unroll
+  for (int k = 0; k < kChains / 2; ++k) s += a2[k].x + a2[k].y;
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
   if (threadIdx.x == 0) {
     cycles[blockIdx.x] = c1 - c0;
@@ -82,17 +100,19 @@ using namespace ap;
 
 extern "C" ap_status ap_pipe_rate(int32_t pipe, double *per_clk_per_sm, double *per_s,
                                   double *sm_mhz) {
-  if (pipe < 0 || pipe > 2 || !per_clk_per_sm || !per_s) return AP_ERR_INVALID_ARG;
+  if (pipe < 0 || pipe > 3 || !per_clk_per_sm || !per_s) return AP_ERR_INVALID_ARG;
   const int sms = num_sms();
   const int grid = sms * kBlocksPerSm;
-  const int iters = pipe == 0 ? 8192 : 1024;
+  const int iters = (pipe == 0 || pipe == 3) ? 8192 : 1024;
   float *sink = nullptr;
   unsigned long long *cyc = nullptr, *ns = nullptr;
   AP_TRY(dmalloc(&sink, (size_t)grid * kThreads));
   cudaError_t e = dmalloc(&cyc, (size_t)grid);
   if (e == cudaSuccess) e = dmalloc(&ns, (size_t)grid);
   void (*k)(int, float *, unsigned long long *, unsigned long long *) =
-      pipe == 0 ? pipe_probe_kernel<0> : pipe == 1 ? pipe_probe_kernel<1> : pipe_probe_kernel<2>;
+      pipe == 0 ? pipe_probe_kernel<0>
+      : pipe == 1 ? pipe_probe_kernel<1>
+      : pipe == 2 ? pipe_probe_kernel<2> : pipe_probe_kernel<3>;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
