@@ -121,7 +121,8 @@ overlap_kernel(Params P) {
   extern __shared__ __align__(16) uint8_t smem[];
   float4 *s_pts = reinterpret_cast<float4 *>(smem);
   float *s_lw = reinterpret_cast<float *>(s_pts + P.stage_cap);
-  float *s_part = (DIM == 3 && HAS_W) ? s_lw + P.stage_cap : s_lw;
+  // 3-D: the weight area also holds the log-weights of the paired layout
+  float *s_part = (DIM == 3) ? s_lw + P.stage_cap : s_lw;
   int16_t *s_rj_item = reinterpret_cast<int16_t *>(s_part + P.max_rj * P.part_items * NV);
   int16_t *s_rj_chunk = s_rj_item + kMaxRowJobs;
   int16_t *s_rj_first = s_rj_chunk + kMaxRowJobs;            // [kMaxBlockItems + 1]
@@ -213,6 +214,36 @@ overlap_kernel(Params P) {
       }
       phase ^= 1;
       if (!ok && threadIdx.x == 0) atomicCAS(P.status, 0, DEV_TIMEOUT_STAGE);
+      if (MODE != COVER) {
+        // The staged block in pairs of points: pair q (points 2q, 2q + 1 of
+        // an item) becomes {x0, x1, y0, y1} {s0, s1, l0, l1} (2-D) or
+        // {x0, x1, y0, y1} {z0, z1, s0, s1} with {l0, l1} in the weight area
+        // (3-D), in place, so one packed operation takes two b-points; a
+        // point past its item's real count gets log-weight -inf (weight 0),
+        // so pairs may run over an odd item's padding.
+        float4 *sp4 = reinterpret_cast<float4 *>(s_pts);
+        float2 *sl2 = reinterpret_cast<float2 *>(s_lw);
+        const int nwarp = blockDim.x >> 5;
+        for (int jl = threadIdx.x >> 5; jl < nJ; jl += nwarp) {
+          const int j = c.j_begin + jl;
+          const int b0 = (int)(P.poff[j] - c.j_pt0), np = (int)(P.poff[j + 1] - P.poff[j]);
+          const int cnt = P.cnt[j];
+          for (int k = lane; 2 * k < np; k += 32) {
+            const int q = (b0 >> 1) + k;
+            const float4 u = sp4[2 * q], v = sp4[2 * q + 1];
+            const bool r0 = 2 * k < cnt, r1 = 2 * k + 1 < cnt;
+            sp4[2 * q] = make_float4(u.x, v.x, u.y, v.y);
+            if (DIM == 3) {
+              sp4[2 * q + 1] = make_float4(u.z, v.z, u.w, v.w);
+              const float2 l = HAS_W ? sl2[q] : make_float2(0.f, 0.f);
+              sl2[q] = make_float2(r0 ? l.x : -INFINITY, r1 ? l.y : -INFINITY);
+            } else {
+              sp4[2 * q + 1] = make_float4(u.z, v.z, r0 ? u.w : -INFINITY, r1 ? v.w : -INFINITY);
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
 
     if (MODE != COVER) {
@@ -291,64 +322,147 @@ overlap_kernel(Params P) {
           float2 accF[R2], cmpF[R2], accX[R2], accY[R2], accT[R2];
 #pragma unroll
           for (int p = 0; p < R2; ++p) { accF[p] = z2; cmpF[p] = z2; accX[p] = z2; accY[p] = z2; accT[p] = z2; }
-          for (int bb0 = b0; bb0 < b1; bb0 += 32) {
-            const int bb1 = min(bb0 + 32, b1);
-            float2 blF[R2], blX[R2], blY[R2], blT[R2];
+          if (!c.use_smem) {
+            // J block read from global memory, one b-point at a time
+            for (int bb0 = b0; bb0 < b1; bb0 += 32) {
+              const int bb1 = min(bb0 + 32, b1);
+              float2 blF[R2], blX[R2], blY[R2], blT[R2];
 #pragma unroll
-            for (int p = 0; p < R2; ++p) { blF[p] = z2; blX[p] = z2; blY[p] = z2; blT[p] = z2; }
+              for (int p = 0; p < R2; ++p) { blF[p] = z2; blX[p] = z2; blY[p] = z2; blT[p] = z2; }
 #pragma unroll 4
-            for (int b = bb0; b < bb1; ++b) {
-              const float4 q = bsrc[b];
-              float lwb, s2b;
-              if (DIM == 3) { s2b = q.w; lwb = HAS_W ? lsrc[b] : 0.f; }
-              else { s2b = q.z; lwb = q.w; }
-              const float2 bx2 = make_float2(q.x, q.x), by2 = make_float2(q.y, q.y);
-              const float2 bs2 = make_float2(s2b, s2b), lw2 = make_float2(lwb, lwb);
+              for (int b = bb0; b < bb1; ++b) {
+                const float4 q = bsrc[b];
+                float lwb, s2b;
+                if (DIM == 3) { s2b = q.w; lwb = HAS_W ? lsrc[b] : 0.f; }
+                else { s2b = q.z; lwb = q.w; }
+                const float2 bx2 = make_float2(q.x, q.x), by2 = make_float2(q.y, q.y);
+                const float2 bs2 = make_float2(s2b, s2b), lw2 = make_float2(lwb, lwb);
+#pragma unroll
+                for (int p = 0; p < R2; ++p) {
+                  const float2 dx = __fadd2_rn(bx2, ntx[p]);          // b - a'
+                  const float2 dy = __fadd2_rn(by2, nty[p]);
+                  float2 d2 = __fmul2_rn(dx, dx);
+                  d2 = __ffma2_rn(dy, dy, d2);
+                  if (DIM == 3) {
+                    const float2 dz = __fadd2_rn(make_float2(q.z, q.z), naz[p]);
+                    d2 = __ffma2_rn(dz, dz, d2);
+                  }
+                  const float2 ns = __fadd2_rn(nas[p], bs2);   // -(s2k_a + s2k_b); SCORE: +
+                  float2 nr, qd = z2;
+                  if (SCORE) {
+                    const float2 q = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
+                    nr = __fmul2_rn(q, make_float2(-q.x, -q.y));        // -1 / s2k
+                    qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
+                                  : __fmul2_rn(q, make_float2(-nr.x, -nr.y));   // q^d
+                  } else {
+                    nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                  }
+                  const float2 arg = __ffma2_rn(d2, nr, lw2);          // lw_b - d^2 / s2k
+                  const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                  blF[p] = SCORE ? __ffma2_rn(e, qd, blF[p]) : __fadd2_rn(blF[p], e);
+                  if (MODE == GRAD) {
+                    // per a-point sums of -e r, -e r x_b and -e r y_b (e nr = -e r);
+                    // the a'-dependent factors are applied once per a-point
+                    const float2 ner = __fmul2_rn(e, nr);
+                    blX[p] = __fadd2_rn(blX[p], ner);
+                    blY[p] = __ffma2_rn(ner, bx2, blY[p]);
+                    blT[p] = __ffma2_rn(ner, by2, blT[p]);
+                  }
+                }
+              }
 #pragma unroll
               for (int p = 0; p < R2; ++p) {
-                const float2 dx = __fadd2_rn(bx2, ntx[p]);          // b - a'
-                const float2 dy = __fadd2_rn(by2, nty[p]);
-                float2 d2 = __fmul2_rn(dx, dx);
-                d2 = __ffma2_rn(dy, dy, d2);
-                if (DIM == 3) {
-                  const float2 dz = __fadd2_rn(make_float2(q.z, q.z), naz[p]);
-                  d2 = __ffma2_rn(dz, dz, d2);
-                }
-                const float2 ns = __fadd2_rn(nas[p], bs2);   // -(s2k_a + s2k_b); SCORE: +
-                float2 nr, qd = z2;
-                if (SCORE) {
-                  const float2 q = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
-                  nr = __fmul2_rn(q, make_float2(-q.x, -q.y));        // -1 / s2k
-                  qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
-                                : __fmul2_rn(q, make_float2(-nr.x, -nr.y));   // q^d
-                } else {
-                  nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
-                }
-                const float2 arg = __ffma2_rn(d2, nr, lw2);          // lw_b - d^2 / s2k
-                const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                blF[p] = SCORE ? __ffma2_rn(e, qd, blF[p]) : __fadd2_rn(blF[p], e);
+                // compensated add of the block sum
+                const float2 yk = __fadd2_rn(blF[p], make_float2(-cmpF[p].x, -cmpF[p].y));
+                const float2 tk = __fadd2_rn(accF[p], yk);
+                const float2 dd = __fadd2_rn(tk, make_float2(-accF[p].x, -accF[p].y));
+                cmpF[p] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
+                accF[p] = tk;
                 if (MODE == GRAD) {
-                  // per a-point sums of -e r, -e r x_b and -e r y_b (e nr = -e r);
-                  // the a'-dependent factors are applied once per a-point
-                  const float2 ner = __fmul2_rn(e, nr);
-                  blX[p] = __fadd2_rn(blX[p], ner);
-                  blY[p] = __ffma2_rn(ner, bx2, blY[p]);
-                  blT[p] = __ffma2_rn(ner, by2, blT[p]);
+                  accX[p] = __fadd2_rn(accX[p], blX[p]);
+                  accY[p] = __fadd2_rn(accY[p], blY[p]);
+                  accT[p] = __fadd2_rn(accT[p], blT[p]);
                 }
               }
             }
+          } else {
+            // J block staged in pairs: each packed operation takes two
+            // b-points against one a-point held in both halves, so no
+            // b-point is broadcast inside the loop
+            const float4 *sp4 = reinterpret_cast<const float4 *>(s_pts);
+            const float2 *sl2 = reinterpret_cast<const float2 *>(s_lw);
+            float2 pF[R], pC[R], pX[R], pY[R], pT[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { pF[r] = z2; pC[r] = z2; pX[r] = z2; pY[r] = z2; pT[r] = z2; }
+            const int q0 = b0 >> 1, q1 = (b1 + 1) >> 1;
+            for (int qb = q0; qb < q1; qb += 16) {
+              const int qe = min(qb + 16, q1);
+              float2 bF[R];                  // this block's f terms (compensated below)
+#pragma unroll
+              for (int r = 0; r < R; ++r) bF[r] = z2;
+#pragma unroll 2
+              for (int q = qb; q < qe; ++q) {
+                const float4 u = sp4[2 * q], v = sp4[2 * q + 1];
+                const float2 X = make_float2(u.x, u.y), Y = make_float2(u.z, u.w);
+                float2 Z = z2, S, L;
+                if (DIM == 3) { Z = make_float2(v.x, v.y); S = make_float2(v.z, v.w); L = sl2[q]; }
+                else { S = make_float2(v.x, v.y); L = make_float2(v.z, v.w); }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                  const int p = r >> 1;
+                  const float ax = (r & 1) ? ntx[p].y : ntx[p].x;
+                  const float ay = (r & 1) ? nty[p].y : nty[p].x;
+                  const float az = (r & 1) ? naz[p].y : naz[p].x;
+                  const float as = (r & 1) ? nas[p].y : nas[p].x;
+                  const float2 dx = __fadd2_rn(X, make_float2(ax, ax));          // b - a'
+                  const float2 dy = __fadd2_rn(Y, make_float2(ay, ay));
+                  float2 d2 = __fmul2_rn(dx, dx);
+                  d2 = __ffma2_rn(dy, dy, d2);
+                  if (DIM == 3) {
+                    const float2 dz = __fadd2_rn(Z, make_float2(az, az));
+                    d2 = __ffma2_rn(dz, dz, d2);
+                  }
+                  const float2 ns = __fadd2_rn(make_float2(as, as), S);   // -(s2k_a + s2k_b); SCORE: +
+                  float2 nr, qd = z2;
+                  if (SCORE) {
+                    const float2 qq = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
+                    nr = __fmul2_rn(qq, make_float2(-qq.x, -qq.y));       // -1 / s2k
+                    qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
+                                  : __fmul2_rn(qq, make_float2(-nr.x, -nr.y));   // q^d
+                  } else {
+                    nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                  }
+                  const float2 arg = __ffma2_rn(d2, nr, L);              // lw_b - d^2 / s2k
+                  const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                  bF[r] = SCORE ? __ffma2_rn(e, qd, bF[r]) : __fadd2_rn(bF[r], e);
+                  if (MODE == GRAD) {
+                    // the gradient's sums go straight to the a-point's totals
+                    const float2 ner = __fmul2_rn(e, nr);
+                    pX[r] = __fadd2_rn(pX[r], ner);
+                    pY[r] = __ffma2_rn(ner, X, pY[r]);
+                    pT[r] = __ffma2_rn(ner, Y, pT[r]);
+                  }
+                }
+              }
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                // compensated add of the block sum (each half on its own)
+                const float2 yk = __fadd2_rn(bF[r], make_float2(-pC[r].x, -pC[r].y));
+                const float2 tk = __fadd2_rn(pF[r], yk);
+                const float2 dd = __fadd2_rn(tk, make_float2(-pF[r].x, -pF[r].y));
+                pC[r] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
+                pF[r] = tk;
+              }
+            }
+            // each a-point's two halves, back in the form of two a-points per
+            // packed value
 #pragma unroll
             for (int p = 0; p < R2; ++p) {
-              // compensated add of the block sum
-              const float2 yk = __fadd2_rn(blF[p], make_float2(-cmpF[p].x, -cmpF[p].y));
-              const float2 tk = __fadd2_rn(accF[p], yk);
-              const float2 dd = __fadd2_rn(tk, make_float2(-accF[p].x, -accF[p].y));
-              cmpF[p] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
-              accF[p] = tk;
+              accF[p] = make_float2(pF[2 * p].x + pF[2 * p].y, pF[2 * p + 1].x + pF[2 * p + 1].y);
               if (MODE == GRAD) {
-                accX[p] = __fadd2_rn(accX[p], blX[p]);
-                accY[p] = __fadd2_rn(accY[p], blY[p]);
-                accT[p] = __fadd2_rn(accT[p], blT[p]);
+                accX[p] = make_float2(pX[2 * p].x + pX[2 * p].y, pX[2 * p + 1].x + pX[2 * p + 1].y);
+                accY[p] = make_float2(pY[2 * p].x + pY[2 * p].y, pY[2 * p + 1].x + pY[2 * p + 1].y);
+                accT[p] = make_float2(pT[2 * p].x + pT[2 * p].y, pT[2 * p + 1].x + pT[2 * p + 1].y);
               }
             }
           }
@@ -555,7 +669,7 @@ cloud_self_kernel(const float4 *__restrict__ pts, const float *__restrict__ lw,
 template <int DIM, bool HAS_W, int MODE, int SCORE = 0>
 cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s) {
   constexpr int NV = (MODE == GRAD) ? 4 : 1;
-  size_t smem = (size_t)P.stage_cap * 16 + ((DIM == 3 && HAS_W) ? (size_t)P.stage_cap * 4 : 0) +
+  size_t smem = (size_t)P.stage_cap * 16 + (DIM == 3 ? (size_t)P.stage_cap * 4 : 0) +
                 (size_t)P.max_rj * P.part_items * NV * 4 +
                 (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
   void (*kern)(Params) = nullptr;

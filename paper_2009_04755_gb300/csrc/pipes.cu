@@ -62,10 +62,8 @@ pipe_probe_kernel(int iters, float *sink, unsigned long long *cycles, unsigned l
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       if (PIPE == 3) {
-        // twice the chains of one packed instruction each: the same results
+        // half as many instructions of two results each: the same results
         // per thread as the scalar probe
-#pragma unroll
-        for (int k = 0; k < kChains / 2; ++k) a2[k] = __ffma2_rn(a2[k], m2, c2);
 #pragma unroll
         for (int k = 0; k < kChains / 2; ++k) a2[k] = __ffma2_rn(a2[k], m2, c2);
       } else {
