@@ -379,6 +379,11 @@ def ours(args):
                        "h2d_bytes_per_step": int(n * D * 4),
                        "d2h_bytes_per_step": int(P * 8), "steps": ksteps,
                        "ms_per_step": e_ms / ksteps}
+        # one more call with the task trace on (after the timed ones)
+        items.set_trace(True)
+        items.load_and_run(Xh, out=out)
+        line["e2e"]["timeline"] = timeline_summary(items.trace())
+        items.set_trace(False)
         Xh = res_h = None
     items.close()
     line["pipe_rates_per_clk_per_sm"] = {k: v["per_clk_per_sm"] for k, v in pipes.items()}
@@ -472,8 +477,13 @@ def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False):
     ms = e0.elapsed_time(e1) / steps
     st = items.stats()
     h2d_gbs = st["h2d_bytes"] / (ms / 1e3) / 1e9
+    # one more run with the task trace on (after the timed ones)
+    items.set_trace(True)
+    items.run_pairs(out=out)
+    timeline = timeline_summary(items.trace())
+    items.set_trace(False)
     line = {"metric": METRIC, "value": P / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
-            "steps": steps, "warmup": max(1, warmup), "ms_per_step": ms,
+            "steps": steps, "warmup": max(1, warmup), "ms_per_step": ms, "timeline": timeline,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
             "config": {"workload": "pearson_ooc_n8192_d3145728", "n_items": n, "dim": D,
@@ -790,6 +800,38 @@ def run_encoded_workload(args):
     items.close()
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timeline_summary(tr):
+    """Busy time per stream, the link rate while copying and how much of the
+    copying overlapped the Gram, from one traced run's tasks (ap_get_trace)."""
+    def union(iv):
+        tot, cur = 0.0, None
+        for a, b in sorted(iv):
+            if cur is None or a > cur[1]:
+                if cur:
+                    tot += cur[1] - cur[0]
+                cur = [a, b]
+            else:
+                cur[1] = max(cur[1], b)
+        return tot + (cur[1] - cur[0] if cur else 0.0)
+
+    def ivs(stage):
+        return [(e["start_ms"], e["end_ms"]) for e in tr if e["stage"] == stage]
+
+    if not tr:
+        return None
+    total = max(e["end_ms"] for e in tr)
+    cp, gr, pp = ivs("copy"), ivs("gram"), ivs("preprocess")
+    both = union([(max(a, c), min(b, d)) for a, b in cp for c, d in gr if min(b, d) > max(a, c)])
+    copy_ms = union(cp)
+    nbytes = sum(e["bytes"] for e in tr)
+    return {"total_ms": total, "tasks": len(tr),
+            "copy_busy_ms": copy_ms, "preprocess_busy_ms": union(pp), "gram_busy_ms": union(gr),
+            "copy_overlapped_by_gram_ms": both,
+            "h2d_gbs_while_copying": nbytes / (copy_ms / 1e3) / 1e9 if copy_ms else None,
+            "first_gram_start_ms": min(a for a, _ in gr) if gr else None,
+            "after_last_copy_ms": total - max(b for _, b in cp) if cp else None}
 
 
 def measure_pipes():

@@ -403,8 +403,8 @@ ap_status ap_set_out_of_core_policy(ap_items *items, int32_t policy);
  * Dp = dim rounded up to 64) under `policy`.  Builds the schedule, checks that
  * every macro pair is computed exactly once with both macros resident, and
  * reports the slots, the macro loads (R = loads / ceil(n/256), Sec. VI-A) and
- * the steps.  AP_OOC_K_SLICED reports 1 slot (its chunk buffer), one load
- * per macro and one step per column chunk.  Errors: AP_ERR_INVALID_ARG (bad
+ * the steps.  AP_OOC_K_SLICED reports 2 slots (its two chunk buffers), one
+ * load per macro and one step per column chunk.  Errors: AP_ERR_INVALID_ARG (bad
  * sizes or policy, NULL outputs, fewer than 3 slots while the set does not
  * fit), AP_ERR_STATE (schedule check failed).
  */
@@ -441,6 +441,43 @@ typedef enum {
  * every bounded device wait (nanoseconds; 0 restores the 2 s default) for
  * the handle's later launches.  Errors: AP_ERR_INVALID_ARG (unknown flag). */
 ap_status ap_set_debug(ap_items *items, int32_t flags, uint64_t wait_budget_ns);
+
+/*
+ * Task trace of the streamed pipelines (the optional profiling flag of
+ * Sec. IV-C that traces the tasks each resource executes, shown as a
+ * timeline in Fig. 4).  With tracing on, the out-of-core column-slice run
+ * (ap_run_pairs on an out-of-core set) and ap_load_and_run record, on each of
+ * their CUDA streams, when every task started and ended: host-to-device
+ * copies (copy stream), pre-processing (pre-processing stream), the Gram and
+ * the final scaling (the caller's stream).  Timing uses CUDA events, so the
+ * traced call stays asynchronous; ap_get_trace waits for the recorded events.
+ */
+typedef enum {
+  AP_STAGE_COPY = 0,        /* host -> device copy of one chunk / macro */
+  AP_STAGE_PREPROCESS = 1,  /* centring and split-BF16 conversion */
+  AP_STAGE_GRAM = 2,        /* tensor-core Gram over one chunk / macro column */
+  AP_STAGE_FINALIZE = 3     /* the pass that scales the pairs */
+} ap_stage;
+
+typedef struct ap_trace_event {
+  int32_t stream;           /* 0 the caller's stream, 1 copies, 2 pre-processing */
+  int32_t stage;            /* ap_stage */
+  int64_t index;            /* column chunk (slices) or 256-item macro (load-and-run) */
+  uint64_t bytes;           /* bytes copied host -> device (AP_STAGE_COPY), else 0 */
+  double start_ms, end_ms;  /* from the start of the traced call */
+} ap_trace_event;
+
+/* ap_set_trace -- turn the task trace of the handle's later calls on (1) or
+ * off (0).  Each traced call replaces the previous call's trace.
+ * Errors: AP_ERR_INVALID_ARG (NULL handle, on not 0/1). */
+ap_status ap_set_trace(ap_items *items, int32_t on);
+
+/* ap_get_trace -- the last traced call's tasks: waits until they have run,
+ * writes min(cap, *count) events to out (host, caller-owned) in the order
+ * they were issued and sets *count to the number recorded (0 when nothing was
+ * traced).  Errors: AP_ERR_INVALID_ARG (NULL handle or count, out NULL with
+ * cap > 0), AP_ERR_CUDA. */
+ap_status ap_get_trace(ap_items *items, ap_trace_event *out, int64_t cap, int64_t *count);
 
 /* Static, NUL-terminated description of a status code. */
 const char *ap_status_string(ap_status s);

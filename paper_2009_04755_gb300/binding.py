@@ -54,6 +54,16 @@ class Plan(ctypes.Structure):
                 ("k_split", ctypes.c_int32), ("mma_ctas", ctypes.c_int32)]
 
 
+class TraceEvent(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_int32), ("stage", ctypes.c_int32), ("index", ctypes.c_int64),
+                ("bytes", ctypes.c_uint64), ("start_ms", ctypes.c_double),
+                ("end_ms", ctypes.c_double)]
+
+
+STAGE_NAMES = ("copy", "preprocess", "gram", "finalize")
+STREAM_NAMES = ("compute", "copy", "preprocess")
+
+
 class APError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -98,6 +108,8 @@ def lib():
             "ap_run_pairs_list": (i32, [vp, i32, i32, vp, vp, i64, vp, vp, vp]),
             "ap_backward_list": (i32, [vp, vp, vp, i64, vp, vp, vp, vp, vp]),
             "ap_ascent_list": (i32, [vp, vp, vp, i64, vp, i32, f32, f32, vp, vp, vp]),
+            "ap_set_trace": (i32, [vp, i32]),
+            "ap_get_trace": (i32, [vp, ctypes.POINTER(TraceEvent), i64, ctypes.POINTER(i64)]),
             "ap_pipe_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -462,6 +474,22 @@ class Items:
         """0: resident set + streamed groups (default); 1: the paper's
         recursive order with LRU eviction; 2: column slices (R = 1)."""
         check(lib().ap_set_out_of_core_policy(self._h, int(policy)), "ap_set_out_of_core_policy")
+
+    def set_trace(self, on: bool = True):
+        """Record the tasks of later streamed runs (out-of-core, load-and-run)
+        per stream with CUDA events (ap_set_trace)."""
+        check(lib().ap_set_trace(self._h, 1 if on else 0), "ap_set_trace")
+
+    def trace(self) -> list:
+        """The last traced call's tasks as dicts: stream, stage, index, bytes,
+        start_ms, end_ms (ap_get_trace; waits for them)."""
+        n = ctypes.c_int64()
+        check(lib().ap_get_trace(self._h, None, 0, ctypes.byref(n)), "ap_get_trace")
+        buf = (TraceEvent * max(n.value, 1))()
+        check(lib().ap_get_trace(self._h, buf, n.value, ctypes.byref(n)), "ap_get_trace")
+        return [{"stream": STREAM_NAMES[e.stream], "stage": STAGE_NAMES[e.stage],
+                 "index": e.index, "bytes": e.bytes, "start_ms": e.start_ms,
+                 "end_ms": e.end_ms} for e in buf[:n.value]]
 
     def set_debug(self, flags: int, wait_budget_ns: int = 0):
         """Failure-path switch (testing) and device wait budget (0 = 2 s)."""

@@ -189,6 +189,34 @@ struct VecStore {
 }  // namespace ap
 
 namespace ap {
+// task trace of a streamed pipeline (ap_set_trace): CUDA events at the start
+// and end of every task, on the stream that runs it
+struct TraceRec {
+  int32_t stream = 0, stage = 0;
+  int64_t index = 0;
+  uint64_t bytes = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+struct Tracer {
+  bool on = false;
+  cudaEvent_t base = nullptr;
+  std::vector<TraceRec> recs;
+  void clear();
+  // a new trace whose time zero is now on s (no-op when tracing is off)
+  cudaError_t start(cudaStream_t s);
+  // open a task on st; returns its record (-1 when off)
+  int begin(int32_t stream, int32_t stage, int64_t index, uint64_t bytes, cudaStream_t st);
+  void end(int rec, cudaStream_t st);
+  ~Tracer() { clear(); }
+};
+// host-side range for tools that show NVTX (the enqueue of one stage)
+struct NvtxRange {
+  explicit NvtxRange(const char *name);
+  ~NvtxRange();
+};
+}  // namespace ap
+
+namespace ap {
 // a captured launch sequence, replayed with cudaGraphLaunch
 struct GraphKey {
   int32_t kind;                    // 1 overlap, 2 coverage, 3 ascent, 4 L2, 5 Bhattacharyya
@@ -248,6 +276,7 @@ struct ap_items {
   uint64_t plan_version = 0;
   uint64_t wait_budget_ns = 0;          // 0 = the default budget
   int32_t debug = 0;                    // failure-path testing switches
+  ap::Tracer trace;                     // task trace of the streamed pipelines
   std::vector<ap::GraphEntry> graphs;
 };
 
@@ -345,6 +374,9 @@ int64_t tc2_pairs();
 // one unit per macro pair over all columns)
 void pair_units(int64_t n, int64_t nchunks, int64_t group, int64_t k_split,
                 std::vector<int32_t> &units);
+// the same for a given list of macro pairs (I, J) in the order to run them
+void pair_units_of(const std::vector<int32_t> &macro_pairs, int64_t nchunks, int64_t group,
+                   int64_t k_split, std::vector<int32_t> &units);
 // out-of-core unit: {A row block, B row blocks (2), I block, J block, chunk
 // begin, chunk end, unused}; chunks are 64 columns of D
 constexpr int kOocTileInts = 8;

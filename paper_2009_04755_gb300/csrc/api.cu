@@ -219,6 +219,7 @@ ap_status create_clouds(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
 // dense vectors
 // ---------------------------------------------------------------------------
 ap_status vec_load(ap_items *it, const float *data, int on_host, cudaStream_t s) {
+  NvtxRange range("load: copy + pre-process");
   VecStore &v = it->vec;
   const bool split = (v.precisions & (1u << AP_PREC_SPLIT_BF16)) != 0;
   const bool f32 = (v.precisions & (1u << AP_PREC_FP32)) != 0;
@@ -457,6 +458,7 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   if ((fn == AP_FN_COSINE) != (it->kind == AP_ITEMS_SPARSE) && fn != AP_FN_COVERAGE)
     return AP_ERR_INVALID_ARG;
   if (precision != AP_PREC_FP32 && precision != AP_PREC_SPLIT_BF16) return AP_ERR_INVALID_ARG;
+  NvtxRange range("ap_run_pairs");
   const bool cloud_fn = fn == AP_FN_OVERLAP || fn == AP_FN_GMM_L2 || fn == AP_FN_BHATTACHARYYA;
   if (cloud_fn && it->kind == AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;
   if (fn == AP_FN_PEARSON && it->kind != AP_ITEMS_VECTOR) return AP_ERR_INVALID_ARG;

@@ -122,11 +122,16 @@ void panel_units(const std::vector<int32_t> &tiles, int64_t nchunks, int64_t gro
 
 void pair_units(int64_t n, int64_t nchunks, int64_t group, int64_t k_split,
                 std::vector<int32_t> &units) {
+  std::vector<int32_t> macro;
+  dc_block_pairs((n + kTcTileN - 1) / kTcTileN, macro);
+  pair_units_of(macro, nchunks, group, k_split, units);
+}
+
+void pair_units_of(const std::vector<int32_t> &macro, int64_t nchunks, int64_t group,
+                   int64_t k_split, std::vector<int32_t> &units) {
   // macro pairs of 256 items; each CTA of a pair takes one 128-item half of
   // the I macro and stages one half of the J macro
   units.clear();
-  std::vector<int32_t> macro;
-  dc_block_pairs((n + kTcTileN - 1) / kTcTileN, macro);
   const int64_t nt = (int64_t)macro.size() / 2;
   k_split = std::max<int64_t>(1, std::min<int64_t>(k_split, nchunks));
   group = std::max<int64_t>(1, group);

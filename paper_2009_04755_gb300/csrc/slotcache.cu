@@ -290,21 +290,28 @@ static ap_status alloc_pool(VecStore &v) {
 
 // Column slices.  The Gram's CTAs leave no room on an SM for the
 // pre-processing kernels, which therefore run between Gram launches; what
-// overlaps the Gram of one chunk is the copy of the next.  So: one hi/lo
-// chunk buffer of all rows and a raw ring of kMacro-row pieces, a whole chunk
-// when the cache allows (at least 64K columns per chunk), else four pieces.
-// Chunk width is a multiple of 64; chunks of equal width cover Dp.
+// overlaps the Gram of one chunk is the copy of the next.  So: two hi/lo
+// chunk buffers of all rows (chunk c + 1 is pre-processed while the Gram of
+// chunk c reads the other one) and a raw ring of kMacro-row pieces, a whole
+// chunk when the cache allows (at least 64K columns per chunk), else four
+// pieces.  Chunk width is a multiple of 64; chunks of equal width cover Dp.
+// The link idles only before the first chunk lands and nothing overlaps the
+// last chunk's pre-processing and Gram, so more, narrower chunks shorten the
+// part of the run that is not copy-bound.
+constexpr int64_t kMinSlices = 12;
 static bool slice_geometry(int64_t n, int64_t Dp, uint64_t budget, int64_t *cols,
                            int64_t *count, int64_t *ring) {
   if (n < 1) return false;
   const int64_t rows = (n + kRowBlock - 1) / kRowBlock * kRowBlock;
   const int64_t pieces = (n + kMacro - 1) / kMacro;
   for (int64_t r : {pieces, std::min<int64_t>(pieces, 4)}) {
-    const uint64_t per_col = 4ull * rows + 4ull * kMacro * r;
+    const uint64_t per_col = 2ull * 4ull * rows + 4ull * kMacro * r;
     const int64_t cmax = (int64_t)(budget / per_col) / kOocChunkCols * kOocChunkCols;
     const bool last = r == std::min<int64_t>(pieces, 4);
     if (cmax >= std::min<int64_t>(Dp, 65536) || (last && cmax >= kOocChunkCols)) {
-      *count = (Dp + cmax - 1) / cmax;
+      // at least kMinSlices chunks while they stay 64K columns wide: the
+      // last chunk's Gram is the part of the run no copy overlaps
+      *count = std::max<int64_t>((Dp + cmax - 1) / cmax, std::min<int64_t>(kMinSlices, Dp / 65536));
       *cols = ((Dp + *count - 1) / *count + kOocChunkCols - 1) / kOocChunkCols * kOocChunkCols;
       *ring = r;
       return true;
@@ -319,31 +326,34 @@ static ap_status alloc_slices(VecStore &v) {
     return AP_ERR_INVALID_ARG;
   const int64_t rows = (v.n + kRowBlock - 1) / kRowBlock * kRowBlock;
   const size_t elems = (size_t)rows * v.slice_cols;
-  AP_TRY(dmalloc(&v.d_slice_hi[0], elems));
-  AP_TRY(dmalloc(&v.d_slice_lo[0], elems));
-  AP_TRY(cudaMemset(v.d_slice_hi[0], 0, elems * 2));
-  AP_TRY(cudaMemset(v.d_slice_lo[0], 0, elems * 2));
-  AP_TRY(make_tc_tensor_maps(v.d_slice_hi[0], v.d_slice_lo[0], v.n, v.slice_cols,
-                             &v.tmap_slice_hi[0], &v.tmap_slice_lo[0]));
-  AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_ready[0], cudaEventDisableTiming));
-  AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_done[0], cudaEventDisableTiming));
+  for (int b = 0; b < 2; ++b) {
+    AP_TRY(dmalloc(&v.d_slice_hi[b], elems));
+    AP_TRY(dmalloc(&v.d_slice_lo[b], elems));
+    AP_TRY(cudaMemset(v.d_slice_hi[b], 0, elems * 2));
+    AP_TRY(cudaMemset(v.d_slice_lo[b], 0, elems * 2));
+    AP_TRY(make_tc_tensor_maps(v.d_slice_hi[b], v.d_slice_lo[b], v.n, v.slice_cols,
+                               &v.tmap_slice_hi[b], &v.tmap_slice_lo[b]));
+    AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_ready[b], cudaEventDisableTiming));
+    AP_TRY(cudaEventCreateWithFlags(&v.ev_slice_done[b], cudaEventDisableTiming));
+  }
   AP_TRY(dmalloc(&v.d_shift, (size_t)v.n));
   AP_TRY(dmalloc(&v.d_delta, (size_t)v.n));
   AP_TRY(dmalloc(&v.d_part_c, (size_t)v.n * kSplitParts));
   AP_TRY_ST(alloc_raw_ring(v, ring, (size_t)kMacro * v.slice_cols));
-  // every tile of the triangle, split-K units in waves over one chunk
+  // every block pair of the triangle on CTA pairs, split-K units in waves
+  // over one chunk
   std::vector<int32_t> tiles, units;
   tc_tiles(v.n, tiles);
   const int64_t nt = (int64_t)tiles.size() / 2;
   const int64_t nch = v.slice_cols / kOocChunkCols;
-  panel_units(tiles, nch, num_sms(), std::max<int32_t>(1, default_k_split(nt, v.slice_cols)),
-              units);
+  pair_units(v.n, nch, tc2_pairs(), std::max<int32_t>(1, default_k_split(nt, v.slice_cols)),
+             units);
   v.n_slice_units = (int64_t)units.size() / kOocTileInts;
   AP_TRY(dmalloc(&v.d_slice_units, std::max<size_t>(units.size(), kOocTileInts)));
   if (!units.empty())
     AP_TRY(cudaMemcpy(v.d_slice_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
   std::vector<int32_t> cover;
-  panel_units(tiles, nch, num_sms(), 1, cover);
+  pair_units(v.n, nch, tc2_pairs(), 1, cover);
   v.n_slice_cover = (int64_t)cover.size() / kOocTileInts;
   AP_TRY(dmalloc(&v.d_slice_cover, std::max<size_t>(cover.size(), kOocTileInts)));
   if (!cover.empty())
@@ -353,18 +363,18 @@ static ap_status alloc_slices(VecStore &v) {
 
 // The column-sliced run: chunk c of every row is copied (strided, in pieces
 // of kMacro rows) on the copy stream, centred on a per-row shift (the mean of
-// the row's first chunk) and split on the prep stream into the chunk buffer
-// once the Gram of chunk c - 1 has finished with it, and the Gram of all
-// tiles over chunk c adds its FP64 partials on s; each item crosses the host
-// link once (R = 1).  The shifted-data identities turn the accumulated sums
-// into the centred Gram at the end.
+// the row's first chunk) and split on the prep stream into chunk buffer c % 2
+// once the Gram of chunk c - 2 has finished with it, and the Gram of all
+// block pairs over chunk c adds its FP64 partials on s; each item crosses the
+// host link once (R = 1).  The shifted-data identities turn the accumulated
+// sums into the centred Gram at the end.
 static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t s) {
   VecStore &v = it->vec;
   const int64_t P = v.n * (v.n - 1) / 2;
   if (coverage) {
-    AP_TRY(launch_gram_tc(v.tmap_slice_hi[0], v.tmap_slice_lo[0], v.n, v.slice_cols, v.d_rs,
-                          v.d_slice_cover, v.n_slice_cover, it->d_queue, it->d_status, v.d_g64,
-                          out, 1, 1, it->wait_budget_ns, it->debug, s));
+    AP_TRY(launch_gram_tc2(v.tmap_slice_hi[0], v.tmap_slice_lo[0], v.n, v.d_rs, v.d_slice_cover,
+                           v.n_slice_cover, it->d_queue, it->d_status, v.d_g64, out, 1, 0,
+                           it->wait_budget_ns, it->debug, s));
     it->stats.tiles = v.n_slice_cover;
     it->stats.item_loads = 0;
     it->stats.reuse_R = 0.0;
@@ -374,28 +384,36 @@ static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t 
   }
   if (!it->prep_stream)
     AP_TRY(cudaStreamCreateWithFlags(&it->prep_stream, cudaStreamNonBlocking));
+  NvtxRange range("out-of-core column slices");
+  Tracer &tr = it->trace;
+  AP_TRY(tr.start(s));
   AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
   AP_TRY(cudaEventRecord(it->ev_a, s));
   AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
   AP_TRY(cudaStreamWaitEvent(it->prep_stream, it->ev_a, 0));
   std::fill(v.ring_used.begin(), v.ring_used.end(), 0);
   int64_t seq = 0;
-  const int b = 0;                          // the chunk buffer
   for (int64_t c = 0; c < v.n_slices; ++c) {
+    const int b = (int)(c & 1);             // the chunk buffer
     const int64_t c0 = c * v.slice_cols;
     const int64_t cols = std::max<int64_t>(0, std::min<int64_t>(v.slice_cols, v.D - c0));
-    if (c >= 1) AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_slice_done[b], 0));
+    NvtxRange chunk_range("chunk: copy + pre-process + Gram");
+    if (c >= 2) AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_slice_done[b], 0));
+    int t_copy = -1, t_prep = -1;
     for (int64_t r0 = 0; r0 < v.n; r0 += kMacro) {
       const int64_t rows = std::min<int64_t>(kMacro, v.n - r0);
       const int64_t rb = seq++ % v.ring;
       float *raw = v.d_raw + (size_t)rb * kMacro * v.slice_cols;
       if (v.ring_used[rb]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[rb], 0));
+      if (r0 == 0)
+        t_copy = tr.begin(1, AP_STAGE_COPY, c, (uint64_t)v.n * cols * 4, it->copy_stream);
       if (cols > 0)
         AP_TRY(cudaMemcpy2DAsync(raw, (size_t)v.slice_cols * 4, v.h_src + (size_t)r0 * v.ld + c0,
                                  (size_t)v.ld * 4, (size_t)cols * 4, (size_t)rows,
                                  cudaMemcpyHostToDevice, it->copy_stream));
       AP_TRY(cudaEventRecord(v.ev_raw_ready[rb], it->copy_stream));
       AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[rb], 0));
+      if (r0 == 0) t_prep = tr.begin(2, AP_STAGE_PREPROCESS, c, 0, it->prep_stream);
       if (c == 0)
         AP_TRY(launch_vec_mean(raw, rows, std::max<int64_t>(cols, 1), v.slice_cols,
                                v.d_shift + r0, it->prep_stream));
@@ -405,17 +423,23 @@ static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t 
       AP_TRY(cudaEventRecord(v.ev_raw_free[rb], it->prep_stream));
       v.ring_used[rb] = 1;
     }
+    tr.end(t_copy, it->copy_stream);
+    tr.end(t_prep, it->prep_stream);
     AP_TRY(cudaEventRecord(v.ev_slice_ready[b], it->prep_stream));
     AP_TRY(cudaStreamWaitEvent(s, v.ev_slice_ready[b], 0));
-    AP_TRY(launch_gram_tc(v.tmap_slice_hi[b], v.tmap_slice_lo[b], v.n, v.slice_cols, v.d_rs,
-                          v.d_slice_units, v.n_slice_units, it->d_queue, it->d_status, v.d_g64,
-                          out, 0, 1, it->wait_budget_ns, it->debug, s));
+    const int t_gram = tr.begin(0, AP_STAGE_GRAM, c, 0, s);
+    AP_TRY(launch_gram_tc2(v.tmap_slice_hi[b], v.tmap_slice_lo[b], v.n, v.d_rs, v.d_slice_units,
+                           v.n_slice_units, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
+                           it->wait_budget_ns, it->debug, s));
+    tr.end(t_gram, s);
     AP_TRY(cudaEventRecord(v.ev_slice_done[b], s));
   }
+  const int t_fin = tr.begin(0, AP_STAGE_FINALIZE, 0, 0, s);
   AP_TRY(launch_slice_finalize(v.d_part, v.d_part_c, v.n, v.D, v.d_delta, v.d_ss, v.d_rs,
                                reinterpret_cast<double *>(out), s));
+  tr.end(t_fin, s);
   it->stats.tiles = v.n_slice_units * v.n_slices;
-  it->stats.tile_m = kTcTileM;
+  it->stats.tile_m = 2 * kTcTileM;
   it->stats.tile_n = kTcTileN;
   it->stats.item_loads = v.n;
   it->stats.reuse_R = 1.0;
@@ -577,11 +601,11 @@ extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t 
   if (policy != AP_OOC_RESIDENT_STREAM && policy != AP_OOC_DC_LRU && policy != AP_OOC_K_SLICED)
     return AP_ERR_INVALID_ARG;
   if (policy == AP_OOC_K_SLICED) {
-    // one chunk buffer; every macro loaded once; one step per column chunk
+    // two chunk buffers; every macro loaded once; one step per column chunk
     int64_t cols, count, ring;
     if (!slice_geometry(n_items, (dim + 63) / 64 * 64, slot_cache_bytes, &cols, &count, &ring))
       return AP_ERR_INVALID_ARG;
-    *n_slots = 1;
+    *n_slots = 2;
     *n_loads = (n_items + kMacro - 1) / kMacro;
     *n_steps = count;
     return AP_OK;
@@ -620,28 +644,23 @@ extern "C" ap_status ap_plan_out_of_core(int64_t n_items, int64_t dim, uint64_t 
 namespace ap {
 
 // Units of the streamed run: column m holds the pairs (a <= m, m) of macros,
-// addressed directly in the resident arrays (row block = item block).
+// addressed directly in the resident arrays (row block = item block), as
+// CTA-pair units in waves like the resident schedule (column ranges of
+// ~16384 columns, two units per SM at least).
 static ap_status build_stream_units(VecStore &v) {
   const int64_t M = (v.n + kMacro - 1) / kMacro;
   const int64_t nch = v.Dp / kOocChunkCols;
   std::vector<int32_t> units;
   v.stream_cols.clear();
   for (int64_t m = 0; m < M; ++m) {
-    std::vector<std::array<int32_t, 3>> tiles;   // ib, rb_b, jb
-    for (int64_t a = 0; a <= m; ++a)
-      for (int h = 0; h < 2; ++h) {
-        const int64_t ib = 2 * a + h, i0 = ib * kRowBlock;
-        const int64_t jmax = std::min<int64_t>(m * kMacro + kMacro, v.n) - 1;
-        if (i0 >= v.n || i0 >= jmax) continue;
-        tiles.push_back({(int32_t)ib, (int32_t)(2 * m), (int32_t)m});
-      }
-    // the column's tiles as split-K units in waves, like the resident
-    // schedule (column ranges of ~16384 columns, two units per SM at least)
-    const int64_t T = (int64_t)tiles.size();
-    std::vector<int32_t> pairs, col_units;
-    for (const auto &t : tiles) { pairs.push_back(t[0]); pairs.push_back(t[2]); }
-    const int64_t ks = std::max<int32_t>(1, default_k_split(T, v.Dp));
-    panel_units(pairs, nch, num_sms(), ks, col_units);
+    std::vector<int32_t> macro, col_units;
+    for (int64_t a = 0; a <= m; ++a) {
+      macro.push_back((int32_t)a);
+      macro.push_back((int32_t)m);
+    }
+    // split-K: the rule of the single-CTA tiles (two 128-row tiles per pair)
+    const int64_t ks = std::max<int32_t>(1, default_k_split(2 * (m + 1), v.Dp));
+    pair_units_of(macro, nch, tc2_pairs(), ks, col_units);
     const int64_t u0 = (int64_t)units.size() / kOocTileInts;
     units.insert(units.end(), col_units.begin(), col_units.end());
     v.stream_cols.push_back({u0, (int64_t)units.size() / kOocTileInts - u0});
@@ -679,6 +698,9 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
   if (!it->prep_stream)
     AP_TRY(cudaStreamCreateWithFlags(&it->prep_stream, cudaStreamNonBlocking));
   const int64_t P = v.n * (v.n - 1) / 2;
+  NvtxRange range("load and run");
+  Tracer &tr = it->trace;
+  AP_TRY(tr.start(s));
   AP_TRY(cudaMemsetAsync(out, 0, (size_t)P * sizeof(double), s));
   // earlier work on s may still read the rows about to be overwritten
   AP_TRY(cudaEventRecord(it->ev_a, s));
@@ -692,24 +714,33 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
     const int64_t r0 = (int64_t)m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
     float *raw = v.d_raw + (size_t)b * kMacro * v.ld;
     if (v.ring_used[b]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[b], 0));
+    const int t_copy = tr.begin(1, AP_STAGE_COPY, (int64_t)m, (uint64_t)rows * v.ld * 4,
+                                it->copy_stream);
     AP_TRY(cudaMemcpyAsync(raw, h + (size_t)r0 * v.ld, (size_t)rows * v.ld * 4,
                            cudaMemcpyHostToDevice, it->copy_stream));
+    tr.end(t_copy, it->copy_stream);
     AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
     AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[b], 0));
+    const int t_prep = tr.begin(2, AP_STAGE_PREPROCESS, (int64_t)m, 0, it->prep_stream);
     AP_TRY(launch_vec_prep(raw, r0, r0, rows, v.D, v.ld, v.Dp, split ? v.d_hi : nullptr,
                            split ? v.d_lo : nullptr, f32 ? v.d_c32 : nullptr, v.d_mu, v.d_part,
                            v.d_partc, v.d_delta_all, v.d_ss, v.d_rs, v.d_recentre,
                            it->prep_stream));
+    tr.end(t_prep, it->prep_stream);
     AP_TRY(cudaEventRecord(v.ev_raw_free[b], it->prep_stream));
     AP_TRY(cudaEventRecord(v.ev_prepped[b], it->prep_stream));
     v.ring_used[b] = 1;
     AP_TRY(cudaStreamWaitEvent(s, v.ev_prepped[b], 0));
-    AP_TRY(launch_gram_tc(v.tmap_hi, v.tmap_lo, v.n, v.Dp, v.d_rs,
-                          v.d_stream_units + v.stream_cols[m].first * kOocTileInts,
-                          v.stream_cols[m].second, it->d_queue, it->d_status, v.d_g64, out, 0, 1,
-                          it->wait_budget_ns, it->debug, s));
+    const int t_gram = tr.begin(0, AP_STAGE_GRAM, (int64_t)m, 0, s);
+    AP_TRY(launch_gram_tc2(v.tmap_hi, v.tmap_lo, v.n, v.d_rs,
+                           v.d_stream_units + v.stream_cols[m].first * kOocTileInts,
+                           v.stream_cols[m].second, it->d_queue, it->d_status, v.d_g64, out, 0,
+                           1, it->wait_budget_ns, it->debug, s));
+    tr.end(t_gram, s);
   }
+  const int t_fin = tr.begin(0, AP_STAGE_FINALIZE, 0, 0, s);
   AP_TRY(launch_pair_finalize(out, v.d_rs, v.d_delta_all, v.n, v.D, s));
+  tr.end(t_fin, s);
   it->stats.item_loads = v.n;
   it->stats.reuse_R = 1.0;
   it->stats.h2d_bytes = (uint64_t)v.n * v.ld * 4;

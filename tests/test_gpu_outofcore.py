@@ -143,9 +143,10 @@ def test_out_of_core_lru_policy(ap, oracle_lib):
 
 
 def _slice_cache(n, cols):
-    """Cache for column chunks of `cols` columns with the four-piece ring."""
+    """Cache for column chunks of `cols` columns: two hi/lo chunk buffers and
+    the four-piece raw ring."""
     rows = (n + 127) // 128 * 128
-    return cols * (4 * rows + 4 * 256 * min(4, -(-n // 256)))
+    return cols * (2 * 4 * rows + 4 * 256 * min(4, -(-n // 256)))
 
 
 def test_out_of_core_column_slices(ap, oracle_lib):
@@ -258,3 +259,56 @@ def test_encoded_items_reject(ap):
             it.run_pairs()
     with pytest.raises(ap.APError):                  # encoded rows need the out-of-core path
         ap.Items.from_encoded(blobs, D, slot_cache_bytes=0)
+
+
+def _check_timeline(tr, n_index, copy_bytes):
+    """Every task once per index and stage, in issue order on its stream,
+    and the dependencies of the pipeline respected on the device clock."""
+    eps = 1e-3
+    by = {}
+    for e in tr:
+        assert 0.0 <= e["start_ms"] <= e["end_ms"] + eps
+        by.setdefault((e["stage"], e["index"]), []).append(e)
+    for stage in ("copy", "preprocess", "gram"):
+        assert sorted(i for (s, i) in by if s == stage) == list(range(n_index)), stage
+    assert [i for (s, i) in by if s == "finalize"] == [0]
+    assert sum(e["bytes"] for e in tr if e["stage"] == "copy") == copy_bytes
+    for stream in ("compute", "copy", "preprocess"):
+        evs = [e for e in tr if e["stream"] == stream]
+        for a, b in zip(evs, evs[1:]):
+            assert b["start_ms"] >= a["end_ms"] - eps, stream
+    for k in range(n_index):
+        c, p, g = by[("copy", k)][0], by[("preprocess", k)][0], by[("gram", k)][0]
+        assert p["start_ms"] >= c["start_ms"] - eps
+        assert g["start_ms"] >= p["end_ms"] - eps
+    fin = by[("finalize", 0)][0]
+    assert fin["start_ms"] >= max(e["end_ms"] for e in tr if e["stage"] == "gram") - eps
+
+
+def test_out_of_core_trace_timeline(ap):
+    """The task trace of Sec. IV-C on the column-slice pipeline: per stream,
+    per chunk, copies / pre-processing / Gram in order, bytes accounted."""
+    n, D = 1000, 3000
+    X = synth.vectors_grouped(n, D, seed=5).pin_memory()
+    cache = max(_slice_cache(n, 1024), 3 * _slot_bytes(D))
+    with ap.Items.from_vectors(X, slot_cache_bytes=cache) as it:
+        it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+        untraced = it.run_pairs().cpu().numpy()
+        assert it.trace() == []
+        it.set_trace(True)
+        got = it.run_pairs().cpu().numpy()
+        tr = it.trace()
+        it.set_trace(False)
+        assert it.trace() == []
+    assert np.array_equal(got, untraced)
+    _check_timeline(tr, 3, n * D * 4)
+
+
+def test_load_and_run_trace_timeline(ap):
+    n, D = 600, 4096
+    X = synth.vectors_grouped(n, D, seed=6)
+    with ap.Items.from_vectors(X.cuda()) as it:
+        it.set_trace(True)
+        it.load_and_run(X.pin_memory())
+        tr = it.trace()
+    _check_timeline(tr, (n + 255) // 256, n * D * 4)

@@ -37,27 +37,27 @@ def test_policy_rejects_unknown(ap):
 
 
 def _slices(n, Dp, budget):
-    """The column-slice geometry: one hi/lo chunk buffer of all rows and a
+    """The column-slice geometry: two hi/lo chunk buffers of all rows and a
     ring of 256-row raw pieces (a whole chunk when that still leaves chunks
     of >= 64K columns, else four pieces)."""
     rows = -(-n // 128) * 128
     pieces = -(-n // 256)
     for r in (pieces, min(pieces, 4)):
-        cmax = budget // (4 * rows + 4 * 256 * r) // 64 * 64
+        cmax = budget // (2 * 4 * rows + 4 * 256 * r) // 64 * 64
         if cmax >= min(Dp, 65536) or (r == min(pieces, 4) and cmax >= 64):
-            count = -(-Dp // cmax)
+            count = max(-(-Dp // cmax), min(12, Dp // 65536))   # >= 12 chunks of >= 64K columns
             return count, -(-(-(-Dp // count)) // 64) * 64
     return None
 
 
 def test_column_slices_plan(ap):
-    """Column slices: one chunk buffer, every macro loaded once (R = 1), one
+    """Column slices: two chunk buffers, every macro loaded once (R = 1), one
     step per column chunk; chunks shrink as the cache does."""
     n, D = 8192, 3 << 20
     macros = (n + 255) // 256
     p = ap.plan_out_of_core(n, D, 48 << 30, ap.AP_OOC_K_SLICED)
-    assert p["slots"] == 1 and p["loads"] == macros
-    assert p["steps"] == _slices(n, D, 48 << 30)[0] == 4
+    assert p["slots"] == 2 and p["loads"] == macros
+    assert p["steps"] == _slices(n, D, 48 << 30)[0] == 12
     small = ap.plan_out_of_core(n, D, 12 << 30, ap.AP_OOC_K_SLICED)
     assert small["steps"] == _slices(n, D, 12 << 30)[0] > p["steps"]
     assert small["loads"] == macros
