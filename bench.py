@@ -408,7 +408,7 @@ RCP_PER_CLK_PER_SM = 16
 OOC_N, OOC_DIM, OOC_CACHE = 8192, 3 << 20, 48 << 30
 
 
-def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False):
+def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False, n=0, D=0, cache=0):
     """Out-of-core correlation: 8192 vectors of 3*2^20 FP32 (96 GiB) in pinned
     host memory streamed through a 48 GiB HBM slot cache (the host's 199 GB of
     RAM cannot hold the 16,384-vector, 192 GiB set pinned; set and cache are
@@ -418,14 +418,15 @@ def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False):
     import synth
     import paper_2009_04755_gb300 as ap
     t_wall = time.perf_counter()
-    n, D = OOC_N, OOC_DIM
+    n, D, cache = n or OOC_N, D or OOC_DIM, cache or OOC_CACHE
     P = n * (n - 1) // 2
     torch.cuda.set_device(0)
     Xh = torch.empty(n, D, dtype=torch.float32, pin_memory=True)
     chunk = 1024
     for r0 in range(0, n, chunk):
-        Xd = synth.vectors_grouped(chunk, D, seed=1000 + r0 // chunk, device="cuda")
-        Xh[r0:r0 + chunk].copy_(Xd)
+        rows = min(chunk, n - r0)
+        Xd = synth.vectors_grouped(rows, D, seed=1000 + r0 // chunk, device="cuda")
+        Xh[r0:r0 + rows].copy_(Xd)
         del Xd
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -459,7 +460,7 @@ def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False):
     torch.cuda.synchronize()
     whole_gbs = n * D * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9
     del probe, ring
-    items = ap.Items.from_vectors(Xh, slot_cache_bytes=OOC_CACHE)
+    items = ap.Items.from_vectors(Xh, slot_cache_bytes=cache)
     if policy:
         items.set_out_of_core_policy(policy)
     out = torch.empty(P, dtype=torch.float64, device="cuda")
@@ -486,8 +487,8 @@ def ooc_record(steps=3, warmup=1, policy=2, no_cpu=False):
             "steps": steps, "warmup": max(1, warmup), "ms_per_step": ms, "timeline": timeline,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16x3/fp32-acc/fp64-norm", "data": "synthetic",
-            "config": {"workload": "pearson_ooc_n8192_d3145728", "n_items": n, "dim": D,
-                       "host_bytes": n * D * 4, "slot_cache_bytes": OOC_CACHE,
+            "config": {"workload": f"pearson_ooc_n{n}_d{D}", "n_items": n, "dim": D,
+                       "host_bytes": n * D * 4, "slot_cache_bytes": cache,
                        "policy": ["resident+streamed", "recursive+lru",
                                   "column-slices"][policy]},
             "reuse_R": st["reuse_R"], "slot_hit_rate": st["slot_hit_rate"],
@@ -532,7 +533,8 @@ def host_ram_bytes():
 
 
 def run_ooc_workload(args):
-    print(json.dumps(ooc_record(args.steps, args.warmup, args.ooc_policy, args.no_cpu)),
+    print(json.dumps(ooc_record(args.steps, args.warmup, args.ooc_policy, args.no_cpu,
+                                args.n, args.dim, int(args.ooc_cache_gib * (1 << 30)))),
           flush=True)
     return 0
 
@@ -1100,6 +1102,9 @@ def main():
     ap.add_argument("--ooc-policy", type=int, default=2, choices=[0, 1, 2],
                     help="out-of-core schedule: 0 resident+streamed, 1 recursive order + LRU, "
                          "2 column slices")
+    ap.add_argument("--ooc-cache-gib", type=float, default=0.0,
+                    help="out-of-core slot cache size override (GiB; with --n/--dim for "
+                         "smaller cases)")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

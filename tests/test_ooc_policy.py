@@ -45,7 +45,7 @@ def _slices(n, Dp, budget):
     for r in (pieces, min(pieces, 4)):
         cmax = budget // (2 * 4 * rows + 4 * 256 * r) // 64 * 64
         if cmax >= min(Dp, 65536) or (r == min(pieces, 4) and cmax >= 64):
-            count = max(-(-Dp // cmax), min(12, Dp // 65536))   # >= 12 chunks of >= 64K columns
+            count = max(-(-Dp // cmax), min(12, Dp // 262144))  # >= 12 chunks of >= 256K columns
             return count, -(-(-(-Dp // count)) // 64) * 64
     return None
 
