@@ -209,8 +209,12 @@ typedef struct ap_plan {
  *   centred on its mean.
  *   Sparse vectors: the CSR arrays copied, FP64 squared norms per row, and
  *   per column chunk of 2048 codes the first entry of every row in it.
- * Inputs may be freed when the call returns (after a stream synchronise),
- * except the out-of-core host source (see slot_cache_bytes).
+ * Host-side planning (block and tile lists, sorting) happens before the call
+ * returns; every copy and kernel of the call is ordered on `stream`, for all
+ * kinds (host sources: pageable memory is staged by the copy calls, pinned
+ * memory is read by the GPU when the stream gets there).  Inputs may be
+ * freed once that work has run (after a stream synchronise), except the
+ * out-of-core host source (see slot_cache_bytes).
  * Errors: AP_ERR_INVALID_ARG (desc/out NULL, negative sizes, bad kind,
  * offsets not non-decreasing, missing arrays, sparse indices not strictly
  * increasing within a row or outside [0, dim)), AP_ERR_OOM, AP_ERR_CUDA.

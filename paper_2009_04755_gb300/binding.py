@@ -233,8 +233,14 @@ class Items:
 
     # ---- construction -------------------------------------------------
     @classmethod
-    def from_clouds(cls, clouds: dict, device: str = "cuda", stream=None) -> "Items":
-        """Clouds dict (numpy or torch): dim, offsets, x, y, z, sigma, weight."""
+    def from_clouds(cls, clouds: dict, device: str = "cuda", stream=None,
+                    sync: bool = True) -> "Items":
+        """Clouds dict (numpy or torch): dim, offsets, x, y, z, sigma, weight.
+        device "cuda": the arrays are copied to the device first; "cpu": the
+        library copies them from (pinned) host memory itself.  The creation
+        runs on `stream` (default: torch's current stream); sync=False
+        returns without waiting for it (the host arrays are kept alive by the
+        handle until it is closed)."""
         import numpy as np
         import torch
         dim = int(clouds["dim"])
@@ -245,23 +251,32 @@ class Items:
             if a is None:
                 return None
             t = torch.as_tensor(np.asarray(a) if not torch.is_tensor(a) else a)
-            return t.to(device=device, dtype=torch.float32).contiguous()
+            t = t.to(device=device, dtype=torch.float32).contiguous()
+            return t.pin_memory() if device == "cpu" else t
 
         arrs = {k: dev(clouds.get(k)) for k in ("x", "y", "z", "sigma", "weight")}
         if dim != 3:
             arrs["z"] = None
         d = ItemsDesc()
         d.kind = AP_ITEMS_CLOUD3D if dim == 3 else AP_ITEMS_CLOUD2D
-        d.data_on_host = 0
+        d.data_on_host = 1 if device == "cpu" else 0
         d.n_items = n
         d.offsets = off.ctypes.data
         for k, t in arrs.items():
             setattr(d, k, None if t is None else t.data_ptr())
+        if device != "cpu":
+            # the copies above ran on torch's current stream
+            ev = torch.cuda.Event()
+            ev.record()
+            (stream or torch.cuda.current_stream()).wait_event(ev)
         h = ctypes.c_void_p()
         check(lib().ap_create_items(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)),
               "ap_create_items")
-        torch.cuda.synchronize()
-        return cls(h, d.kind, n)
+        if sync:
+            torch.cuda.synchronize()
+        obj = cls(h, d.kind, n)
+        obj._keep = (arrs, off)                 # sources until the handle is closed
+        return obj
 
     @classmethod
     def from_vectors(cls, X, precisions=(AP_PREC_SPLIT_BF16,), stream=None,

@@ -474,7 +474,7 @@ void dfree(T *&p) {
 
 struct CloudPlanChoice { int32_t block_items, block_pts, reg_r; bool sorted; };
 CloudPlanChoice choose_cloud_plan(const CloudStore &c);
-ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch);
+ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch, cudaStream_t s = nullptr);
 // smallest a-points-per-lane that keeps the largest item within the row jobs
 int32_t min_reg_r(const CloudStore &c);
 

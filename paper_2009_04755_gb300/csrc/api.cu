@@ -106,7 +106,7 @@ CloudPlanChoice choose_cloud_plan(const CloudStore &c) {
   return ch;
 }
 
-ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
+ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch, cudaStream_t s) {
   CloudStore &c = it->cl;
   std::vector<int64_t> cnt(c.n);
   for (int64_t s = 0; s < c.n; ++s) cnt[s] = c.h_size[c.h_perm[s]];
@@ -120,9 +120,10 @@ ap_status build_cloud_plan(ap_items *it, const CloudPlanChoice &ch) {
   dfree(c.d_tiles);
   AP_TRY(dmalloc(&c.d_bstart, bstart.size()));
   AP_TRY(dmalloc(&c.d_tiles, std::max<size_t>(tiles.size(), 2)));
-  AP_TRY(cudaMemcpy(c.d_bstart, bstart.data(), bstart.size() * 4, cudaMemcpyHostToDevice));
+  // pageable sources: the copies are staged before the calls return
+  AP_TRY(cudaMemcpyAsync(c.d_bstart, bstart.data(), bstart.size() * 4, cudaMemcpyHostToDevice, s));
   if (!tiles.empty())
-    AP_TRY(cudaMemcpy(c.d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
+    AP_TRY(cudaMemcpyAsync(c.d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s));
   c.h_bstart = bstart;
   c.max_rj = max_row_jobs(bstart, cnt, 32LL * ch.reg_r);
   c.n_tiles = (int64_t)tiles.size() / 2;
@@ -178,41 +179,41 @@ ap_status create_clouds(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   AP_TRY(dmalloc(&c.d_poff, c.n + 1));
   AP_TRY(dmalloc(&c.d_cnt, std::max<int64_t>(c.n, 1)));
   AP_TRY(dmalloc(&c.d_perm, std::max<int64_t>(c.n, 1)));
-  AP_TRY(cudaMemcpy(c.d_poff, c.h_poff.data(), (c.n + 1) * 8, cudaMemcpyHostToDevice));
+  // everything below is ordered on the caller's stream; host sources must
+  // stay valid until that stream has run it (pageable memory is staged by
+  // the copy calls themselves)
+  AP_TRY(cudaMemcpyAsync(c.d_poff, c.h_poff.data(), (c.n + 1) * 8, cudaMemcpyHostToDevice, s));
   if (c.n > 0) {
-    AP_TRY(cudaMemcpy(c.d_cnt, cnt32.data(), c.n * 4, cudaMemcpyHostToDevice));
-    AP_TRY(cudaMemcpy(c.d_perm, c.h_perm.data(), c.n * 4, cudaMemcpyHostToDevice));
+    AP_TRY(cudaMemcpyAsync(c.d_cnt, cnt32.data(), c.n * 4, cudaMemcpyHostToDevice, s));
+    AP_TRY(cudaMemcpyAsync(c.d_perm, c.h_perm.data(), c.n * 4, cudaMemcpyHostToDevice, s));
   }
 
   if (total > 0) {
-    // source arrays on the device (temporary copies when they are host memory)
+    // source arrays on the device (temporary copies when they are host
+    // memory), from the stream-ordered allocator and freed on the stream
     const float *src[5] = {d->x, d->y, c.dim == 3 ? d->z : nullptr, d->sigma, d->weight};
     float *tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int64_t *d_src_off = nullptr;
-    ap_status st = AP_OK;
-    cudaError_t e = dmalloc(&d_src_off, c.n + 1);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_src_off), (c.n + 1) * 8, s);
     if (e == cudaSuccess)
-      e = cudaMemcpy(d_src_off, off, (c.n + 1) * 8, cudaMemcpyHostToDevice);
+      e = cudaMemcpyAsync(d_src_off, off, (c.n + 1) * 8, cudaMemcpyHostToDevice, s);
     for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
-      if (!src[k]) continue;
-      if (d->data_on_host) {
-        e = dmalloc(&tmp[k], total);
-        if (e == cudaSuccess)
-          e = cudaMemcpy(tmp[k], src[k], total * 4, cudaMemcpyHostToDevice);
-      }
+      if (!src[k] || !d->data_on_host) continue;
+      e = cudaMallocAsync(reinterpret_cast<void **>(&tmp[k]), total * 4, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp[k], src[k], total * 4, cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess) {
       auto pick = [&](int k) -> const float * { return d->data_on_host ? tmp[k] : src[k]; };
       e = launch_cloud_pack(pick(0), pick(1), pick(2), pick(3), pick(4), d_src_off, c.d_perm,
                             c.d_poff, c.n, c.dim, c.d_pts, c.d_lw, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
-    if (e != cudaSuccess) st = from_cuda(e);
-    for (int k = 0; k < 5; ++k) dfree(tmp[k]);
-    dfree(d_src_off);
-    if (st != AP_OK) return st;
+    for (int k = 0; k < 5; ++k)
+      if (tmp[k]) cudaFreeAsync(tmp[k], s);
+    if (d_src_off) cudaFreeAsync(d_src_off, s);
+    if (e != cudaSuccess) return from_cuda(e);
   }
-  return build_cloud_plan(it, ch);
+  return build_cloud_plan(it, ch, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -391,9 +391,9 @@ overlap_kernel(Params P) {
             // b-point is broadcast inside the loop
             const float4 *sp4 = reinterpret_cast<const float4 *>(s_pts);
             const float2 *sl2 = reinterpret_cast<const float2 *>(s_lw);
-            float2 pF[R], pC[R], pX[R], pY[R], pT[R];
+            float2 pF[R], pC[R], pY[R], pT[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) { pF[r] = z2; pC[r] = z2; pX[r] = z2; pY[r] = z2; pT[r] = z2; }
+            for (int r = 0; r < R; ++r) { pF[r] = z2; pC[r] = z2; pY[r] = z2; pT[r] = z2; }
             const int q0 = b0 >> 1, q1 = (b1 + 1) >> 1;
             for (int qb = q0; qb < q1; qb += 16) {
               const int qe = min(qb + 16, q1);
@@ -436,11 +436,12 @@ overlap_kernel(Params P) {
                   const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
                   bF[r] = SCORE ? __ffma2_rn(e, qd, bF[r]) : __fadd2_rn(bF[r], e);
                   if (MODE == GRAD) {
-                    // the gradient's sums go straight to the a-point's totals
+                    // the gradient needs only u = sum -e r d' (d' = b - a'):
+                    // df/dt ~ u and df/dtheta ~ nty u_x - ntx u_y, the
+                    // b x b terms of sum e r (x_b d'_y - y_b d'_x) cancelling
                     const float2 ner = __fmul2_rn(e, nr);
-                    pX[r] = __fadd2_rn(pX[r], ner);
-                    pY[r] = __ffma2_rn(ner, X, pY[r]);
-                    pT[r] = __ffma2_rn(ner, Y, pT[r]);
+                    pY[r] = __ffma2_rn(ner, dx, pY[r]);
+                    pT[r] = __ffma2_rn(ner, dy, pT[r]);
                   }
                 }
               }
@@ -455,12 +456,13 @@ overlap_kernel(Params P) {
               }
             }
             // each a-point's two halves, back in the form of two a-points per
-            // packed value
+            // packed value; the gradient's terms as the epilogue below takes
+            // them (S x a' + Sx = u, so S = 0 with Sx, Sy = u)
 #pragma unroll
             for (int p = 0; p < R2; ++p) {
               accF[p] = make_float2(pF[2 * p].x + pF[2 * p].y, pF[2 * p + 1].x + pF[2 * p + 1].y);
               if (MODE == GRAD) {
-                accX[p] = make_float2(pX[2 * p].x + pX[2 * p].y, pX[2 * p + 1].x + pX[2 * p + 1].y);
+                accX[p] = z2;
                 accY[p] = make_float2(pY[2 * p].x + pY[2 * p].y, pY[2 * p + 1].x + pY[2 * p + 1].y);
                 accT[p] = make_float2(pT[2 * p].x + pT[2 * p].y, pT[2 * p + 1].x + pT[2 * p + 1].y);
               }

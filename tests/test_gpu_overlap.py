@@ -113,3 +113,17 @@ def test_overlap_symmetric_at_identity(ap):
         p = ap.pair_index(i, j, n)
         q = ap.pair_index(n - 1 - j, n - 1 - i, n)
         assert abs(f[p] - g[q]) <= 1e-5 * abs(f[p])
+
+
+def test_clouds_created_on_a_side_stream_from_pinned_host(ap, oracle_lib):
+    # creation copies and packs on the caller's stream: the pairs run on the
+    # same stream with no host synchronisation in between
+    c = synth.clouds_uniform(n=40, dim=2, size=(20, 60), seed=12)
+    pi, pj = oracle_lib.all_pairs(40)
+    ref, kappa, bound = oracle_lib.overlap(c, pi, pj, with_cond=True)
+    s = torch.cuda.Stream()
+    it = ap.Items.from_clouds(c, device="cpu", stream=s, sync=False)
+    out = it.run_pairs(stream=s)
+    s.synchronize()
+    check_overlap(out.cpu().numpy(), ref, kappa, bound, "side stream")
+    it.close()
