@@ -409,8 +409,10 @@ ap_status set_vector_plan(ap_items *it, int32_t k_split, int32_t mma_ctas = 0);
 // first use (api.cu)
 ap_status ensure_score_storage(ap_items *it, int score, cudaStream_t s);
 // pair lists (pairlist.cu): Pearson of listed pairs over the resident rows
+// (pairs sorted by row block, pos = each result's position in the caller's list)
 cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
-                                const int32_t *pj, int64_t n_pairs, double *out, cudaStream_t s);
+                                const int32_t *pj, const int32_t *pos, int64_t n_pairs,
+                                double *out, cudaStream_t s);
 
 // clouds (overlap.cu)
 cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,

@@ -13,6 +13,11 @@
 // BF16 or FP32 copy), the same three products per column as the tensor-core
 // Gram, summed in FP32 over 64 column blocks per lane and in FP64 after:
 //   r_k = (sum_c c_a c_b - D delta_a delta_b) rs_a rs_b.
+// The blocked layout puts a row's 32-column pieces 8 KB apart, so a row is
+// read as scattered 64-byte pieces; the list is therefore run sorted by the
+// row blocks of its two items (smaller item first: r is symmetric), so that
+// the warps in flight read pieces of the same 8 KB blocks, and each result
+// goes back to its list position.
 // Sparse rows merge their sorted codes (one CTA per pair).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -33,9 +38,9 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(kListThreads)
 pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *__restrict__ lo,
                     const float *__restrict__ c32, int64_t Dp, const int32_t *__restrict__ pi,
-                    const int32_t *__restrict__ pj, int64_t n_pairs,
-                    const double *__restrict__ rs, const double *__restrict__ delta, int64_t D,
-                    double *__restrict__ out) {
+                    const int32_t *__restrict__ pj, const int32_t *__restrict__ pos,
+                    int64_t n_pairs, const double *__restrict__ rs,
+                    const double *__restrict__ delta, int64_t D, double *__restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_pairs;
@@ -89,7 +94,7 @@ pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *_
     }
     acc += (double)part;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[k] = (acc - (double)D * delta[a] * delta[b]) * rs[a] * rs[b];
+    if (lane == 0) out[pos[k]] = (acc - (double)D * delta[a] * delta[b]) * rs[a] * rs[b];
   }
 }
 
@@ -206,21 +211,46 @@ ap_status device_pairs(const int32_t *pi, const int32_t *pj, int64_t n_pairs, cu
   return AP_OK;
 }
 
+// the listed vector pairs sorted by the row blocks of their items (smaller
+// item first), with their list positions: [a...][b...][position...] on the
+// device (the host copy goes through a pageable buffer, staged by the call)
+ap_status device_pairs_by_block(const int32_t *pi, const int32_t *pj, int64_t n_pairs,
+                                cudaStream_t s, int32_t **d_idx) {
+  std::vector<uint64_t> key((size_t)n_pairs);
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    const uint32_t a = (uint32_t)std::min(pi[k], pj[k]), b = (uint32_t)std::max(pi[k], pj[k]);
+    const uint64_t blocks = ((uint64_t)(a / kRowBlock) << 16) | (uint64_t)(b / kRowBlock);
+    key[k] = (blocks << 32) | (uint64_t)k;     // row blocks < 2^16 (n <= INT32_MAX / 2)
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int32_t> h((size_t)n_pairs * 3);
+  for (int64_t q = 0; q < n_pairs; ++q) {
+    const int64_t k = (int64_t)(key[q] & 0xffffffffu);
+    h[q] = std::min(pi[k], pj[k]);
+    h[n_pairs + q] = std::max(pi[k], pj[k]);
+    h[2 * n_pairs + q] = (int32_t)k;
+  }
+  AP_TRY(dmalloc(d_idx, h.size()));
+  AP_TRY(cudaMemcpyAsync(*d_idx, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
+  return AP_OK;
+}
+
 }  // namespace
 
 cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
-                                const int32_t *pj, int64_t n_pairs, double *out, cudaStream_t s) {
+                                const int32_t *pj, const int32_t *pos, int64_t n_pairs,
+                                double *out, cudaStream_t s) {
   if (n_pairs <= 0) return cudaSuccess;
   const int64_t need = (n_pairs + (kListThreads / 32) - 1) / (kListThreads / 32);
   const int grid = (int)std::min<int64_t>(need, (int64_t)num_sms() * 8);
   if (split)
     pearson_list_kernel<true><<<grid, kListThreads, 0, s>>>(v.d_hi, v.d_lo, nullptr, v.Dp, pi, pj,
-                                                            n_pairs, v.d_rs, v.d_delta_all, v.D,
-                                                            out);
+                                                            pos, n_pairs, v.d_rs, v.d_delta_all,
+                                                            v.D, out);
   else
     pearson_list_kernel<false><<<grid, kListThreads, 0, s>>>(nullptr, nullptr, v.d_c32, v.Dp, pi,
-                                                             pj, n_pairs, v.d_rs, v.d_delta_all,
-                                                             v.D, out);
+                                                             pj, pos, n_pairs, v.d_rs,
+                                                             v.d_delta_all, v.D, out);
   return cudaGetLastError();
 }
 
@@ -254,7 +284,8 @@ extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precisi
       if ((split && !v.d_hi) || (!split && !v.d_c32)) return AP_ERR_STATE;
     }
     int32_t *d_idx = nullptr;
-    ap_status st = device_pairs(pi, pj, n_pairs, s, &d_idx);
+    ap_status st = sparse ? device_pairs(pi, pj, n_pairs, s, &d_idx)
+                          : device_pairs_by_block(pi, pj, n_pairs, s, &d_idx);
     cudaError_t e = cudaSuccess;
     if (st == AP_OK) {
       if (sparse) {
@@ -265,8 +296,8 @@ extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precisi
                                                            reinterpret_cast<double *>(out));
         e = cudaGetLastError();
       } else {
-        e = launch_pearson_list(it->vec, split, d_idx, d_idx + n_pairs, n_pairs,
-                                reinterpret_cast<double *>(out), s);
+        e = launch_pearson_list(it->vec, split, d_idx, d_idx + n_pairs, d_idx + 2 * n_pairs,
+                                n_pairs, reinterpret_cast<double *>(out), s);
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the index buffer goes
       st = e == cudaSuccess ? AP_OK : from_cuda(e);

@@ -309,7 +309,7 @@ constexpr int kF32K = 16;
 constexpr int kF32Pad = 4;
 
 template <int COVER>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
                 const double *__restrict__ rs, const int32_t *__restrict__ tiles,
                 int64_t n_tiles, int32_t *queue, void *out, const double *__restrict__ delta,
@@ -319,7 +319,7 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
   __shared__ int s_tile;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int64_t nk = Dp / kF32K;
+  const int nk = (int)(Dp / kF32K);          // < 2^27 k-blocks (int32 keeps registers free)
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(queue, 1);
@@ -341,7 +341,7 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 
     float4 ra[2], rb[2];
-    auto gload = [&](int64_t kb) {
+    auto gload = [&](int kb) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         ra[h] = __ldg(ablk + kb * 512 + tid + 256 * h);
@@ -362,8 +362,8 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
     gload(0);
     sstore(0);
     __syncthreads();
-    for (int64_t kb = 0; kb < nk; ++kb) {
-      const int buf = (int)(kb & 1);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int buf = kb & 1;
       if (kb + 1 < nk) gload(kb + 1);
 #pragma unroll
       for (int k = 0; k < kF32K; ++k) {
@@ -508,7 +508,16 @@ cudaError_t launch_gram_f32(const float *C, int64_t n, int64_t Dp, const double 
   if (n_tiles <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  int64_t grid = (int64_t)num_sms();
+  // as many persistent CTAs as fit (two per SM: 16 warps keep the FMA pipe
+  // issuing where 8 left it idle a third of the time)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, coverage ? gram_f32_kernel<1> : gram_f32_kernel<0>, 256, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > n_tiles) grid = n_tiles;
   if (coverage)
     gram_f32_kernel<1><<<(int)grid, 256, 0, s>>>(C, n, Dp, rs, tiles, n_tiles, queue, out, delta,
