@@ -330,6 +330,10 @@ cudaError_t launch_pair_correct(double *out, const double *rs, const double *del
 // out[p] = (out[p] - D delta_i delta_j) rs_i rs_j over the packed triangle
 cudaError_t launch_pair_finalize(double *out, const double *rs, const double *delta, int64_t n,
                                  int64_t D, cudaStream_t s);
+// per-row shifts of rows read where they are (X may be pinned host memory
+// the device can address): the mean of 32 evenly spaced runs of 32 values
+cudaError_t launch_vec_shift_runs(const float *X, int64_t n, int64_t D, int64_t ld,
+                                  double *shift, cudaStream_t s);
 // one column chunk [.., cols) of rows row0.., centred on per-row shifts (the
 // rows' blocked copies hold cols_p >= cols columns); FP64 partials of
 // sum c^2 and sum c are set (first_chunk) or accumulated per row

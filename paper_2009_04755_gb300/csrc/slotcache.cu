@@ -368,7 +368,8 @@ static ap_status alloc_slices(VecStore &v) {
 
 // The column-sliced run: chunk c of every row is copied (strided, in pieces
 // of kMacro rows) on the copy stream, centred on a per-row shift (the mean of
-// the row's first chunk) and split on the prep stream into chunk buffer c % 2
+// 32 runs of 32 values spread over the whole row, so that a trend or a period
+// does not leave the shift far from the row's mean) and split on the prep stream into chunk buffer c % 2
 // once the Gram of chunk c - 2 has finished with it, and the Gram of all
 // block pairs over chunk c adds its FP64 partials on s; each item crosses the
 // host link once (R = 1).  The shifted-data identities turn the accumulated
@@ -396,6 +397,15 @@ static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t 
   AP_TRY(cudaEventRecord(it->ev_a, s));
   AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
   AP_TRY(cudaStreamWaitEvent(it->prep_stream, it->ev_a, 0));
+  // per-row shifts from samples spread over each whole row, read from the
+  // page-locked source where it is; where the source is not mapped into the
+  // device's address space, the mean of the row's first chunk
+  const float *d_src = nullptr;
+  if (cudaHostGetDevicePointer((void **)&d_src, (void *)v.h_src, 0) != cudaSuccess) {
+    cudaGetLastError();
+    d_src = nullptr;
+  }
+  if (d_src) AP_TRY(launch_vec_shift_runs(d_src, v.n, v.D, v.ld, v.d_shift, it->prep_stream));
   std::fill(v.ring_used.begin(), v.ring_used.end(), 0);
   int64_t seq = 0;
   for (int64_t c = 0; c < v.n_slices; ++c) {
@@ -419,7 +429,7 @@ static ap_status run_slices(ap_items *it, void *out, int coverage, cudaStream_t 
       AP_TRY(cudaEventRecord(v.ev_raw_ready[rb], it->copy_stream));
       AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[rb], 0));
       if (r0 == 0) t_prep = tr.begin(2, AP_STAGE_PREPROCESS, c, 0, it->prep_stream);
-      if (c == 0)
+      if (c == 0 && !d_src)
         AP_TRY(launch_vec_mean(raw, rows, std::max<int64_t>(cols, 1), v.slice_cols,
                                v.d_shift + r0, it->prep_stream));
       AP_TRY(launch_vec_split_slice(raw, r0, rows, cols, v.slice_cols, v.slice_cols, v.d_shift,

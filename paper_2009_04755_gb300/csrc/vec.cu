@@ -241,6 +241,37 @@ __global__ void vec_shift_kernel(const float *__restrict__ X, int64_t n, int64_t
   }
 }
 
+// The shift of rows read straight from pinned host memory (column slices,
+// before any chunk is copied): the mean of kShiftRuns evenly spaced runs of 32
+// consecutive values, so that each warp load is one 128-byte request across
+// the host link; a trend or a period is averaged over the whole row, not
+// only over its first chunk.  One warp per row; D < 1024: every value.
+constexpr int kShiftRuns = 32;
+__global__ void vec_shift_runs_kernel(const float *__restrict__ X, int64_t n, int64_t D,
+                                     int64_t ld, double *__restrict__ shift) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const bool all = D < 32 * kShiftRuns;
+  const int64_t gap = all ? 32 : D / kShiftRuns;            // >= 32 when sampling
+  const int64_t runs = all ? (D + 31) / 32 : kShiftRuns;
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+       row += warps) {
+    const float *x = X + row * ld;
+    double acc = 0.0;
+    int64_t cnt = 0;
+#pragma unroll 8
+    for (int64_t r = 0; r < runs; ++r) {
+      const int64_t k = r * gap + lane;
+      if (k < D) { acc += (double)x[k]; ++cnt; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) shift[row] = acc / (double)cnt;
+  }
+}
+
 // A row whose shift misses its mean by D delta^2 > ss / 64 is centred again
 // on the exact mean: the shifted rows' common part D delta_i delta_j then
 // stays below 1/64 of sqrt(ss_i ss_j), so it adds nothing measurable to the
@@ -412,6 +443,14 @@ cudaError_t launch_vec_mean(const float *X, int64_t n, int64_t D, int64_t ld, do
   const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   if (vec4) vec_mean_kernel<true><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu);
   else vec_mean_kernel<false><<<grid, kStatsThreads, 0, s>>>(X, n, D, ld, mu);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_shift_runs(const float *X, int64_t n, int64_t D, int64_t ld,
+                                  double *shift, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int sg = (int)std::min<int64_t>((n + 7) / 8, 65535);
+  vec_shift_runs_kernel<<<sg, 256, 0, s>>>(X, n, D, ld, shift);
   return cudaGetLastError();
 }
 

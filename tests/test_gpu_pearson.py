@@ -276,6 +276,8 @@ def test_pearson_offsets_and_trends(ap, oracle_lib):
         check(it.run_pairs().cpu().numpy(), tol, "out-of-core resident+streamed")
         it.set_out_of_core_policy(ap.binding.AP_OOC_DC_LRU)
         check(it.run_pairs().cpu().numpy(), tol, "out-of-core recursive+LRU")
+        it.set_out_of_core_policy(ap.binding.AP_OOC_K_SLICED)
+        check(it.run_pairs().cpu().numpy(), tol, "out-of-core column slices")
         assert it.last_device_error() == 0
     with ap.Items.from_vectors(Xp) as it:
         check(it.load_and_run(Xp).cpu().numpy(), tol, "load and run")
