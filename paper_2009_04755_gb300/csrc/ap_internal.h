@@ -139,6 +139,7 @@ struct VecStore {
   int64_t n_rows_alloc = 0;         // rows rounded up to the row block
   __nv_bfloat16 *d_hi = nullptr, *d_lo = nullptr;              // [n][Dp]
   float *d_c32 = nullptr;                                      // [n][Dp]
+  uint32_t *d_rows = nullptr;       // [n][Dp] row-major copy for long pair lists
   float *d_stage = nullptr;         // raw rows staged from the host
   int64_t stage_rows = 0;
   // out-of-core mode: HBM slot cache of 256-item macros
@@ -413,10 +414,12 @@ ap_status set_vector_plan(ap_items *it, int32_t k_split, int32_t mma_ctas = 0);
 // first use (api.cu)
 ap_status ensure_score_storage(ap_items *it, int score, cudaStream_t s);
 // pair lists (pairlist.cu): Pearson of listed pairs over the resident rows
-// (pairs sorted by row block, pos = each result's position in the caller's list)
-cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
+// (pairs sorted by row block, pos = each result's position in the caller's
+// list; blocks = the n_blocks distinct row blocks the list touches)
+cudaError_t launch_pearson_list(VecStore &v, bool split, const int32_t *pi,
                                 const int32_t *pj, const int32_t *pos, int64_t n_pairs,
-                                double *out, cudaStream_t s);
+                                const int32_t *blocks, int64_t n_blocks, double *out,
+                                cudaStream_t s);
 
 // clouds (overlap.cu)
 cudaError_t launch_overlap(const CloudStore &cs, const float *params, float *out,

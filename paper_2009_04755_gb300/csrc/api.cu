@@ -61,6 +61,7 @@ void free_items(ap_items *it) {
   dfree(c.d_self);
   VecStore &v = it->vec;
   dfree(v.d_mu); dfree(v.d_ss); dfree(v.d_rs); dfree(v.d_part); dfree(v.d_hi); dfree(v.d_lo); dfree(v.d_c32);
+  dfree(v.d_rows);
   dfree(v.d_partc); dfree(v.d_delta_all); dfree(v.d_recentre);
   dfree(v.d_stage); dfree(v.d_tiles_tc); dfree(v.d_tiles_f32); dfree(v.d_g64);
   dfree(v.d_panel_units); dfree(v.d_pair_units); dfree(v.d_pair_whole);

@@ -98,6 +98,144 @@ pearson_list_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *_
   }
 }
 
+// Long lists read a row-major copy instead.  Scattered 64-byte pieces reach
+// about a quarter of the HBM copy rate; when the list reads the rows it
+// touches several times over, the call first copies the touched row blocks
+// into a row-major buffer of one 4-byte word per column (a split column's hi
+// and lo bf16 packed, hi in the low half; or the FP32 value), streaming the
+// blocked arrays once, and each pair then reads two contiguous rows.
+constexpr int kRowsCols = 128;                  // columns per relayout item
+constexpr int kRowsSlot = kRowBlock * 64 + 64;  // one staged 8 KB block + 64 B,
+                                                // so slots start 16 banks apart
+constexpr int kRowsSmem = 8 * kRowsSlot;
+constexpr int kRowsThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+// Item (row block rb, column group g): the 128 columns from g * 128 of every
+// row of the block.  SPLIT: slots 0-3 hold hi's 32-column blocks, 4-7 lo's;
+// FP32: slots 0-7 hold 16-column blocks.  Each warp then writes whole rows'
+// 512-byte pieces.
+template <bool SPLIT>
+__global__ void __launch_bounds__(kRowsThreads, 3)
+list_rows_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *__restrict__ lo,
+                 const float *__restrict__ c32, int64_t n, int64_t Dp,
+                 const int32_t *__restrict__ blocks, int64_t n_blocks,
+                 uint32_t *__restrict__ rows) {
+  extern __shared__ __align__(16) uint8_t st[];
+  const int64_t groups = (Dp + kRowsCols - 1) / kRowsCols;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kblk = SPLIT ? kTcKBlock : kF32KBlock;
+  const int64_t nkb = Dp / kblk;
+  for (int64_t w = blockIdx.x; w < n_blocks * groups; w += gridDim.x) {
+    const int64_t rb = blocks[w / groups], col0 = (w % groups) * kRowsCols;
+    const int cols = (int)(Dp - col0 < kRowsCols ? Dp - col0 : kRowsCols);   // 128 or 64
+    const int per_slot = cols / kblk;            // staged blocks per array
+    // 512 16-byte chunks per staged block
+    for (int c = threadIdx.x; c < 8 * 512; c += kRowsThreads) {
+      const int slot = c >> 9, off = (c & 511) * 16;
+      const int kbl = SPLIT ? (slot & 3) : slot;
+      if (kbl >= per_slot) continue;
+      const int64_t kb = col0 / kblk + kbl;
+      const uint8_t *src;
+      if (SPLIT) {
+        const __nv_bfloat16 *arr = slot < 4 ? hi : lo;
+        src = reinterpret_cast<const uint8_t *>(arr + (size_t)(rb * nkb + kb) * kRowBlock * kblk);
+      } else {
+        src = reinterpret_cast<const uint8_t *>(c32 + (size_t)(rb * nkb + kb) * kRowBlock * kblk);
+      }
+      cp_async16(st + slot * kRowsSlot + off, src + off);
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int c4 = lane * 4;                     // this lane's four columns
+    if (c4 < cols) {
+      for (int r = warp; r < kRowBlock; r += kRowsThreads / 32) {
+        const int64_t row = rb * kRowBlock + r;
+        if (row >= n) break;
+        uint4 o;
+        if (SPLIT) {
+          const int kbl = c4 / kTcKBlock, c = c4 % kTcKBlock;
+          const uint2 h = *reinterpret_cast<const uint2 *>(st + kbl * kRowsSlot +
+                                                           (r * kTcKBlock + c) * 2);
+          const uint2 l = *reinterpret_cast<const uint2 *>(st + (4 + kbl) * kRowsSlot +
+                                                           (r * kTcKBlock + c) * 2);
+          o.x = __byte_perm(h.x, l.x, 0x5410);
+          o.y = __byte_perm(h.x, l.x, 0x7632);
+          o.z = __byte_perm(h.y, l.y, 0x5410);
+          o.w = __byte_perm(h.y, l.y, 0x7632);
+        } else {
+          const int kbl = c4 / kF32KBlock, c = c4 % kF32KBlock;
+          o = *reinterpret_cast<const uint4 *>(st + kbl * kRowsSlot + (r * kF32KBlock + c) * 4);
+        }
+        *reinterpret_cast<uint4 *>(rows + (size_t)row * Dp + col0 + c4) = o;
+      }
+    }
+    __syncthreads();                             // before the slots are refilled
+  }
+}
+
+// One warp per listed pair over the row-major copy: lane l takes four
+// consecutive columns of every 128, four such loads per row in flight; FP32
+// partials over 64 columns per lane, then FP64, as the blocked kernel.
+template <bool SPLIT>
+__global__ void __launch_bounds__(kListThreads)
+pearson_rows_kernel(const uint32_t *__restrict__ rows, int64_t Dp, const int32_t *__restrict__ pi,
+                    const int32_t *__restrict__ pj, const int32_t *__restrict__ pos,
+                    int64_t n_pairs, const double *__restrict__ rs,
+                    const double *__restrict__ delta, int64_t D, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t nq = Dp / 4;                     // 16-byte words per row
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_pairs;
+       k += warps) {
+    const int64_t a = pi[k], b = pj[k];
+    const uint4 *ra = reinterpret_cast<const uint4 *>(rows + (size_t)a * Dp);
+    const uint4 *rb = reinterpret_cast<const uint4 *>(rows + (size_t)b * Dp);
+    double acc = 0.0;
+    float part = 0.f;
+    for (int64_t q0 = 0, t = 0; q0 < nq; q0 += 128, ++t) {
+      uint4 va[4], vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t q = q0 + u * 32 + lane;
+        const bool in = q < nq;
+        va[u] = in ? __ldg(ra + q) : make_uint4(0u, 0u, 0u, 0u);
+        vb[u] = in ? __ldg(rb + q) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t wa[4] = {va[u].x, va[u].y, va[u].z, va[u].w};
+        const uint32_t wb[4] = {vb[u].x, vb[u].y, vb[u].z, vb[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (SPLIT) {
+            const float ha = __uint_as_float(wa[e] << 16), la = __uint_as_float(wa[e] & 0xffff0000u);
+            const float hb = __uint_as_float(wb[e] << 16), lb = __uint_as_float(wb[e] & 0xffff0000u);
+            part = fmaf(ha, hb, part);
+            part = fmaf(ha, lb, part);
+            part = fmaf(la, hb, part);
+          } else {
+            part = fmaf(__uint_as_float(wa[e]), __uint_as_float(wb[e]), part);
+          }
+        }
+      }
+      if ((t & 3) == 3) {                        // 64 columns per lane
+        acc += (double)part;
+        part = 0.f;
+      }
+    }
+    acc += (double)part;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[pos[k]] = (acc - (double)D * delta[a] * delta[b]) * rs[a] * rs[b];
+  }
+}
+
 // Sparse rows (strictly increasing codes): one CTA per listed pair, each
 // thread merging an even slice of row a's entries against row b from the
 // first code of b at or after its slice (a binary search), so a pair costs
@@ -212,10 +350,12 @@ ap_status device_pairs(const int32_t *pi, const int32_t *pj, int64_t n_pairs, cu
 }
 
 // the listed vector pairs sorted by the row blocks of their items (smaller
-// item first), with their list positions: [a...][b...][position...] on the
-// device (the host copy goes through a pageable buffer, staged by the call)
+// item first), with their list positions, then the distinct row blocks the
+// list touches: [a...][b...][position...][block...] on the device (the host
+// copy goes through a pageable buffer, staged by the call)
 ap_status device_pairs_by_block(const int32_t *pi, const int32_t *pj, int64_t n_pairs,
-                                cudaStream_t s, int32_t **d_idx) {
+                                int64_t n, cudaStream_t s, int32_t **d_idx,
+                                int64_t *n_blocks) {
   std::vector<uint64_t> key((size_t)n_pairs);
   for (int64_t k = 0; k < n_pairs; ++k) {
     const uint32_t a = (uint32_t)std::min(pi[k], pj[k]), b = (uint32_t)std::max(pi[k], pj[k]);
@@ -224,12 +364,17 @@ ap_status device_pairs_by_block(const int32_t *pi, const int32_t *pj, int64_t n_
   }
   std::sort(key.begin(), key.end());
   std::vector<int32_t> h((size_t)n_pairs * 3);
+  std::vector<uint8_t> touched((size_t)((n + kRowBlock - 1) / kRowBlock), 0);
   for (int64_t q = 0; q < n_pairs; ++q) {
     const int64_t k = (int64_t)(key[q] & 0xffffffffu);
     h[q] = std::min(pi[k], pj[k]);
     h[n_pairs + q] = std::max(pi[k], pj[k]);
     h[2 * n_pairs + q] = (int32_t)k;
+    touched[h[q] / kRowBlock] = touched[h[n_pairs + q] / kRowBlock] = 1;
   }
+  for (size_t r = 0; r < touched.size(); ++r)
+    if (touched[r]) h.push_back((int32_t)r);
+  *n_blocks = (int64_t)h.size() - n_pairs * 3;
   AP_TRY(dmalloc(d_idx, h.size()));
   AP_TRY(cudaMemcpyAsync(*d_idx, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
   return AP_OK;
@@ -237,12 +382,46 @@ ap_status device_pairs_by_block(const int32_t *pi, const int32_t *pj, int64_t n_
 
 }  // namespace
 
-cudaError_t launch_pearson_list(const VecStore &v, bool split, const int32_t *pi,
+cudaError_t launch_pearson_list(VecStore &v, bool split, const int32_t *pi,
                                 const int32_t *pj, const int32_t *pos, int64_t n_pairs,
-                                double *out, cudaStream_t s) {
+                                const int32_t *blocks, int64_t n_blocks, double *out,
+                                cudaStream_t s) {
   if (n_pairs <= 0) return cudaSuccess;
   const int64_t need = (n_pairs + (kListThreads / 32) - 1) / (kListThreads / 32);
   const int grid = (int)std::min<int64_t>(need, (int64_t)num_sms() * 8);
+  // the copy streams 2 x 128 rows per touched block at about the HBM rate;
+  // it pays once the list reads those rows, in 64-byte pieces at about a
+  // quarter of that rate, more than kRowsPairsPerBlock pairs per block
+  constexpr int64_t kRowsPairsPerBlock = 32;
+  if (n_pairs >= kRowsPairsPerBlock * n_blocks) {
+    if (!v.d_rows && dmalloc(&v.d_rows, (size_t)v.n * v.Dp) != cudaSuccess) {
+      cudaGetLastError();                       // no room: the blocked kernel
+      v.d_rows = nullptr;
+    }
+  }
+  if (v.d_rows && n_pairs >= kRowsPairsPerBlock * n_blocks) {
+    const cudaError_t e =
+        split ? cudaFuncSetAttribute(list_rows_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem)
+              : cudaFuncSetAttribute(list_rows_kernel<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kRowsSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t items = n_blocks * ((v.Dp + kRowsCols - 1) / kRowsCols);
+    const int rgrid = (int)std::min<int64_t>(items, (int64_t)num_sms() * 3 * 16);
+    if (split) {
+      list_rows_kernel<true><<<rgrid, kRowsThreads, kRowsSmem, s>>>(
+          v.d_hi, v.d_lo, nullptr, v.n, v.Dp, blocks, n_blocks, v.d_rows);
+      pearson_rows_kernel<true><<<grid, kListThreads, 0, s>>>(v.d_rows, v.Dp, pi, pj, pos, n_pairs,
+                                                              v.d_rs, v.d_delta_all, v.D, out);
+    } else {
+      list_rows_kernel<false><<<rgrid, kRowsThreads, kRowsSmem, s>>>(
+          nullptr, nullptr, v.d_c32, v.n, v.Dp, blocks, n_blocks, v.d_rows);
+      pearson_rows_kernel<false><<<grid, kListThreads, 0, s>>>(v.d_rows, v.Dp, pi, pj, pos,
+                                                               n_pairs, v.d_rs, v.d_delta_all,
+                                                               v.D, out);
+    }
+    return cudaGetLastError();
+  }
   if (split)
     pearson_list_kernel<true><<<grid, kListThreads, 0, s>>>(v.d_hi, v.d_lo, nullptr, v.Dp, pi, pj,
                                                             pos, n_pairs, v.d_rs, v.d_delta_all,
@@ -284,8 +463,9 @@ extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precisi
       if ((split && !v.d_hi) || (!split && !v.d_c32)) return AP_ERR_STATE;
     }
     int32_t *d_idx = nullptr;
+    int64_t n_blocks = 0;
     ap_status st = sparse ? device_pairs(pi, pj, n_pairs, s, &d_idx)
-                          : device_pairs_by_block(pi, pj, n_pairs, s, &d_idx);
+                          : device_pairs_by_block(pi, pj, n_pairs, n, s, &d_idx, &n_blocks);
     cudaError_t e = cudaSuccess;
     if (st == AP_OK) {
       if (sparse) {
@@ -297,7 +477,8 @@ extern "C" ap_status ap_run_pairs_list(ap_items *it, int32_t fn, int32_t precisi
         e = cudaGetLastError();
       } else {
         e = launch_pearson_list(it->vec, split, d_idx, d_idx + n_pairs, d_idx + 2 * n_pairs,
-                                n_pairs, reinterpret_cast<double *>(out), s);
+                                n_pairs, d_idx + 3 * n_pairs, n_blocks,
+                                reinterpret_cast<double *>(out), s);
       }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // before the index buffer goes
       st = e == cudaSuccess ? AP_OK : from_cuda(e);

@@ -135,11 +135,15 @@ def test_autograd_list(ap, oracle_lib):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-def test_pearson_list(ap, oracle_lib, prec):
+@pytest.mark.parametrize("m", [2000, 40])
+def test_pearson_list(ap, oracle_lib, prec, m):
+    """2000 pairs over three row blocks read a row-major copy of the rows
+    (the last 128-column group holds 64, the last block 44 rows); 40 pairs
+    read the blocked arrays in place."""
     n, D = 300, 12325
     X = synth.vectors_grouped(n, D, seed=31) + torch.linspace(-5, 5, n)[:, None]
     X = X.contiguous()
-    pi, pj = _random_list(n, 2000, seed=prec)
+    pi, pj = _random_list(n, m, seed=prec)
     ref = oracle_lib.pearson(X.numpy(), pi, pj)
     with ap.Items.from_vectors(X.cuda(), precisions=(prec,)) as it:
         got = it.run_pairs_list(pi, pj, ap.AP_FN_PEARSON, prec).cpu().numpy()
