@@ -38,6 +38,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "ap_internal.h"
 
 namespace ap {
@@ -395,65 +397,78 @@ overlap_kernel(Params P) {
 #pragma unroll
             for (int r = 0; r < R; ++r) { pF[r] = z2; pC[r] = z2; pY[r] = z2; pT[r] = z2; }
             const int q0 = b0 >> 1, q1 = (b1 + 1) >> 1;
-            for (int qb = q0; qb < q1; qb += 16) {
-              const int qe = min(qb + 16, q1);
-              float2 bF[R];                  // this block's f terms (compensated below)
+            // RE of the lane's R a-points: a chunk whose real points fit
+            // the first half (an item's last chunk) sweeps only that half
+            // (the scores' items are large: their last chunks are a small
+            // share, and the second copy of the loop costs them registers)
+            auto sweep = [&](auto re) {
+              constexpr int RE = decltype(re)::value;
+              for (int qb = q0; qb < q1; qb += 16) {
+                const int qe = min(qb + 16, q1);
+                float2 bF[RE];                  // this block's f terms (compensated below)
 #pragma unroll
-              for (int r = 0; r < R; ++r) bF[r] = z2;
+                for (int r = 0; r < RE; ++r) bF[r] = z2;
 #pragma unroll 2
-              for (int q = qb; q < qe; ++q) {
-                const float4 u = sp4[2 * q], v = sp4[2 * q + 1];
-                const float2 X = make_float2(u.x, u.y), Y = make_float2(u.z, u.w);
-                float2 Z = z2, S, L;
-                if (DIM == 3) { Z = make_float2(v.x, v.y); S = make_float2(v.z, v.w); L = sl2[q]; }
-                else { S = make_float2(v.x, v.y); L = make_float2(v.z, v.w); }
+                for (int q = qb; q < qe; ++q) {
+                  const float4 u = sp4[2 * q], v = sp4[2 * q + 1];
+                  const float2 X = make_float2(u.x, u.y), Y = make_float2(u.z, u.w);
+                  float2 Z = z2, S, L;
+                  if (DIM == 3) { Z = make_float2(v.x, v.y); S = make_float2(v.z, v.w); L = sl2[q]; }
+                  else { S = make_float2(v.x, v.y); L = make_float2(v.z, v.w); }
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                  const int p = r >> 1;
-                  const float ax = (r & 1) ? ntx[p].y : ntx[p].x;
-                  const float ay = (r & 1) ? nty[p].y : nty[p].x;
-                  const float az = (r & 1) ? naz[p].y : naz[p].x;
-                  const float as = (r & 1) ? nas[p].y : nas[p].x;
-                  const float2 dx = __fadd2_rn(X, make_float2(ax, ax));          // b - a'
-                  const float2 dy = __fadd2_rn(Y, make_float2(ay, ay));
-                  float2 d2 = __fmul2_rn(dx, dx);
-                  d2 = __ffma2_rn(dy, dy, d2);
-                  if (DIM == 3) {
-                    const float2 dz = __fadd2_rn(Z, make_float2(az, az));
-                    d2 = __ffma2_rn(dz, dz, d2);
-                  }
-                  const float2 ns = __fadd2_rn(make_float2(as, as), S);   // -(s2k_a + s2k_b); SCORE: +
-                  float2 nr, qd = z2;
-                  if (SCORE) {
-                    const float2 qq = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
-                    nr = __fmul2_rn(qq, make_float2(-qq.x, -qq.y));       // -1 / s2k
-                    qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
-                                  : __fmul2_rn(qq, make_float2(-nr.x, -nr.y));   // q^d
-                  } else {
-                    nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
-                  }
-                  const float2 arg = __ffma2_rn(d2, nr, L);              // lw_b - d^2 / s2k
-                  const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
-                  bF[r] = SCORE ? __ffma2_rn(e, qd, bF[r]) : __fadd2_rn(bF[r], e);
-                  if (MODE == GRAD) {
-                    // the gradient needs only u = sum -e r d' (d' = b - a'):
-                    // df/dt ~ u and df/dtheta ~ nty u_x - ntx u_y, the
-                    // b x b terms of sum e r (x_b d'_y - y_b d'_x) cancelling
-                    const float2 ner = __fmul2_rn(e, nr);
-                    pY[r] = __ffma2_rn(ner, dx, pY[r]);
-                    pT[r] = __ffma2_rn(ner, dy, pT[r]);
+                  for (int r = 0; r < RE; ++r) {
+                    const int p = r >> 1;
+                    const float ax = (r & 1) ? ntx[p].y : ntx[p].x;
+                    const float ay = (r & 1) ? nty[p].y : nty[p].x;
+                    const float az = (r & 1) ? naz[p].y : naz[p].x;
+                    const float as = (r & 1) ? nas[p].y : nas[p].x;
+                    const float2 dx = __fadd2_rn(X, make_float2(ax, ax));          // b - a'
+                    const float2 dy = __fadd2_rn(Y, make_float2(ay, ay));
+                    float2 d2 = __fmul2_rn(dx, dx);
+                    d2 = __ffma2_rn(dy, dy, d2);
+                    if (DIM == 3) {
+                      const float2 dz = __fadd2_rn(Z, make_float2(az, az));
+                      d2 = __ffma2_rn(dz, dz, d2);
+                    }
+                    const float2 ns = __fadd2_rn(make_float2(as, as), S);   // -(s2k_a + s2k_b); SCORE: +
+                    float2 nr, qd = z2;
+                    if (SCORE) {
+                      const float2 qq = make_float2(rsq_approx(ns.x), rsq_approx(ns.y));
+                      nr = __fmul2_rn(qq, make_float2(-qq.x, -qq.y));       // -1 / s2k
+                      qd = DIM == 2 ? make_float2(-nr.x, -nr.y)
+                                    : __fmul2_rn(qq, make_float2(-nr.x, -nr.y));   // q^d
+                    } else {
+                      nr = make_float2(rcp_approx(ns.x), rcp_approx(ns.y));
+                    }
+                    const float2 arg = __ffma2_rn(d2, nr, L);              // lw_b - d^2 / s2k
+                    const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+                    bF[r] = SCORE ? __ffma2_rn(e, qd, bF[r]) : __fadd2_rn(bF[r], e);
+                    if (MODE == GRAD) {
+                      // the gradient needs only u = sum -e r d' (d' = b - a'):
+                      // df/dt ~ u and df/dtheta ~ nty u_x - ntx u_y, the
+                      // b x b terms of sum e r (x_b d'_y - y_b d'_x) cancelling
+                      const float2 ner = __fmul2_rn(e, nr);
+                      pY[r] = __ffma2_rn(ner, dx, pY[r]);
+                      pT[r] = __ffma2_rn(ner, dy, pT[r]);
+                    }
                   }
                 }
-              }
 #pragma unroll
-              for (int r = 0; r < R; ++r) {
-                // compensated add of the block sum (each half on its own)
-                const float2 yk = __fadd2_rn(bF[r], make_float2(-pC[r].x, -pC[r].y));
-                const float2 tk = __fadd2_rn(pF[r], yk);
-                const float2 dd = __fadd2_rn(tk, make_float2(-pF[r].x, -pF[r].y));
-                pC[r] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
-                pF[r] = tk;
+                for (int r = 0; r < RE; ++r) {
+                  // compensated add of the block sum (each half on its own)
+                  const float2 yk = __fadd2_rn(bF[r], make_float2(-pC[r].x, -pC[r].y));
+                  const float2 tk = __fadd2_rn(pF[r], yk);
+                  const float2 dd = __fadd2_rn(tk, make_float2(-pF[r].x, -pF[r].y));
+                  pC[r] = __fadd2_rn(dd, make_float2(-yk.x, -yk.y));
+                  pF[r] = tk;
+                }
               }
+            };
+            if constexpr (SCORE == 0) {
+              if (a_end - a_begin <= 16 * R) sweep(std::integral_constant<int, R / 2>());
+              else sweep(std::integral_constant<int, R>());
+            } else {
+              sweep(std::integral_constant<int, R>());
             }
             // each a-point's two halves, back in the form of two a-points per
             // packed value; the gradient's terms as the epilogue below takes
