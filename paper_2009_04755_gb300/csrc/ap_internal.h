@@ -168,8 +168,11 @@ struct VecStore {
   cudaEvent_t ev_slice_ready[2] = {nullptr, nullptr}, ev_slice_done[2] = {nullptr, nullptr};
   // streamed load-and-run of a resident set: per macro column m, the split-K
   // units of the pairs (a <= m, m) on the resident blocked arrays
+  // With stream_chunks > 1 the columns go in chunks of stream_chunk_cols,
+  // and entry c * macros + m holds the units of macro column m over chunk c
   int32_t *d_stream_units = nullptr;
   std::vector<std::pair<int64_t, int64_t>> stream_cols;   // (first unit, units)
+  int64_t stream_chunks = 0, stream_chunk_cols = 0;
   // tile plans
   int32_t *d_tiles_tc = nullptr;  int64_t n_tiles_tc = 0;
   // k_split > 0: the tiles run as split-K units in waves (panel_units)
@@ -331,6 +334,14 @@ cudaError_t launch_pair_correct(double *out, const double *rs, const double *del
 // out[p] = (out[p] - D delta_i delta_j) rs_i rs_j over the packed triangle
 cudaError_t launch_pair_finalize(double *out, const double *rs, const double *delta, int64_t n,
                                  int64_t D, cudaStream_t s);
+// columns [col0, col0 + width) of rows row0.. (cols of them real, staged
+// with leading dimension ld) centred on per-row shifts and split into blocked
+// copies Dl columns wide; FP64 partials of c and c^2 accumulated per row
+cudaError_t launch_vec_split_cols(const float *X, int64_t row0, int64_t n, int64_t cols,
+                                  int64_t ld, int64_t width, int64_t col0, int64_t Dl,
+                                  const double *shift, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                  float *c32, double *part, double *part_c, int first_chunk,
+                                  cudaStream_t s);
 // per-row shifts of rows read where they are (X may be pinned host memory
 // the device can address): the mean of 32 evenly spaced runs of 32 values
 cudaError_t launch_vec_shift_runs(const float *X, int64_t n, int64_t D, int64_t ld,

@@ -661,35 +661,66 @@ namespace ap {
 // Units of the streamed run: column m holds the pairs (a <= m, m) of macros,
 // addressed directly in the resident arrays (row block = item block), as
 // CTA-pair units in waves like the resident schedule (column ranges of
-// ~16384 columns, two units per SM at least).
-static ap_status build_stream_units(VecStore &v) {
+// ~16384 columns, two units per SM at least).  With C column chunks, each
+// (chunk, column) entry holds those pairs over the chunk's columns only.
+static ap_status build_stream_units(VecStore &v, int64_t C) {
   const int64_t M = (v.n + kMacro - 1) / kMacro;
-  const int64_t nch = v.Dp / kOocChunkCols;
+  const int64_t ccols = C > 1 ? (v.Dp + C - 1) / C : v.Dp;
+  v.stream_chunk_cols = (ccols + kOocChunkCols - 1) / kOocChunkCols * kOocChunkCols;
+  v.stream_chunks = C;
   std::vector<int32_t> units;
   v.stream_cols.clear();
-  for (int64_t m = 0; m < M; ++m) {
-    std::vector<int32_t> macro, col_units;
-    for (int64_t a = 0; a <= m; ++a) {
-      macro.push_back((int32_t)a);
-      macro.push_back((int32_t)m);
+  for (int64_t c = 0; c < C; ++c) {
+    const int64_t c0 = c * v.stream_chunk_cols;
+    const int64_t w = std::min<int64_t>(v.stream_chunk_cols, v.Dp - c0);
+    const int64_t nch = w / kOocChunkCols, off = c0 / kOocChunkCols;
+    for (int64_t m = 0; m < M; ++m) {
+      std::vector<int32_t> macro, col_units;
+      for (int64_t a = 0; a <= m; ++a) {
+        macro.push_back((int32_t)a);
+        macro.push_back((int32_t)m);
+      }
+      // split-K: the rule of the single-CTA tiles (two 128-row tiles per pair)
+      const int64_t ks = std::max<int32_t>(1, default_k_split(2 * (m + 1), w));
+      pair_units_of(macro, nch, tc2_pairs(), ks, col_units);
+      for (size_t u = 0; u < col_units.size(); u += kOocTileInts) {
+        col_units[u + 6] += (int32_t)off;
+        col_units[u + 7] += (int32_t)off;
+      }
+      const int64_t u0 = (int64_t)units.size() / kOocTileInts;
+      units.insert(units.end(), col_units.begin(), col_units.end());
+      v.stream_cols.push_back({u0, (int64_t)units.size() / kOocTileInts - u0});
     }
-    // split-K: the rule of the single-CTA tiles (two 128-row tiles per pair)
-    const int64_t ks = std::max<int32_t>(1, default_k_split(2 * (m + 1), v.Dp));
-    pair_units_of(macro, nch, tc2_pairs(), ks, col_units);
-    const int64_t u0 = (int64_t)units.size() / kOocTileInts;
-    units.insert(units.end(), col_units.begin(), col_units.end());
-    v.stream_cols.push_back({u0, (int64_t)units.size() / kOocTileInts - u0});
   }
+  dfree(v.d_stream_units);
   AP_TRY(dmalloc(&v.d_stream_units, std::max<size_t>(units.size(), kOocTileInts)));
   if (!units.empty())
     AP_TRY(cudaMemcpy(v.d_stream_units, units.data(), units.size() * 4, cudaMemcpyHostToDevice));
   return AP_OK;
 }
 
+// Column chunks for the streamed run: rows of 2 MiB or more go in chunks of
+// whole 1 MiB pieces (at most 8), so that each chunk's Gram is spread over
+// its copies and only the last chunk's last columns follow the last copy;
+// strided pieces of 1 MiB copy at the link's full rate, shorter ones do not.
+static int64_t stream_chunks_for(const VecStore &v) {
+  constexpr int64_t kPieceCols = (1 << 20) / 4;
+  if (v.D < 2 * kPieceCols) return 1;
+  return std::min<int64_t>(8, v.D / kPieceCols);
+}
+
 ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStream_t s) {
   VecStore &v = it->vec;
-  if (!v.d_stream_units) {
-    ap_status st = build_stream_units(v);
+  // column chunks need the shifts before the first chunk: sampled over the
+  // whole rows from the page-locked source, where the device can read it
+  const float *d_src = nullptr;
+  if (cudaHostGetDevicePointer((void **)&d_src, (void *)h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    d_src = nullptr;
+  }
+  const int64_t C = d_src ? stream_chunks_for(v) : 1;
+  if (!v.d_stream_units || v.stream_chunks != C) {
+    ap_status st = build_stream_units(v, C);
     if (st != AP_OK) return st;
   }
   if (!v.d_raw) {
@@ -722,6 +753,61 @@ ap_status stream_load_and_run(ap_items *it, const float *h, double *out, cudaStr
   AP_TRY(cudaStreamWaitEvent(it->copy_stream, it->ev_a, 0));
   AP_TRY(cudaStreamWaitEvent(it->prep_stream, it->ev_a, 0));
   const bool split = v.d_hi != nullptr, f32 = v.d_c32 != nullptr;
+  if (C > 1) {
+    // chunk c of macro m: a strided copy of its rows' columns, split into
+    // the resident arrays at those columns (FP64 sums of c and c^2 added up
+    // over the chunks), then the pairs (a <= m, m) over the chunk
+    AP_TRY(launch_vec_shift_runs(d_src, v.n, v.D, v.ld, v.d_mu, it->prep_stream));
+    const int64_t M = (v.n + kMacro - 1) / kMacro;
+    int64_t seq = 0;
+    for (int64_t c = 0; c < C; ++c) {
+      const int64_t c0 = c * v.stream_chunk_cols;
+      const int64_t w = std::min<int64_t>(v.stream_chunk_cols, v.Dp - c0);
+      const int64_t cols = std::max<int64_t>(0, std::min<int64_t>(w, v.D - c0));
+      for (int64_t m = 0; m < M; ++m, ++seq) {
+        const int64_t b = seq % v.ring;
+        const int64_t r0 = m * kMacro, rows = std::min<int64_t>(kMacro, v.n - r0);
+        float *raw = v.d_raw + (size_t)b * kMacro * v.ld;
+        if (v.ring_used[b]) AP_TRY(cudaStreamWaitEvent(it->copy_stream, v.ev_raw_free[b], 0));
+        const int t_copy = tr.begin(1, AP_STAGE_COPY, seq, (uint64_t)rows * cols * 4,
+                                    it->copy_stream);
+        if (cols > 0)
+          AP_TRY(cudaMemcpy2DAsync(raw, (size_t)w * 4, h + (size_t)r0 * v.ld + c0,
+                                   (size_t)v.ld * 4, (size_t)cols * 4, (size_t)rows,
+                                   cudaMemcpyHostToDevice, it->copy_stream));
+        tr.end(t_copy, it->copy_stream);
+        AP_TRY(cudaEventRecord(v.ev_raw_ready[b], it->copy_stream));
+        AP_TRY(cudaStreamWaitEvent(it->prep_stream, v.ev_raw_ready[b], 0));
+        const int t_prep = tr.begin(2, AP_STAGE_PREPROCESS, seq, 0, it->prep_stream);
+        AP_TRY(launch_vec_split_cols(raw, r0, rows, cols, w, w, c0, v.Dp, v.d_mu,
+                                     split ? v.d_hi : nullptr, split ? v.d_lo : nullptr,
+                                     f32 ? v.d_c32 : nullptr, v.d_part, v.d_partc, c == 0 ? 1 : 0,
+                                     it->prep_stream));
+        tr.end(t_prep, it->prep_stream);
+        AP_TRY(cudaEventRecord(v.ev_raw_free[b], it->prep_stream));
+        AP_TRY(cudaEventRecord(v.ev_prepped[b], it->prep_stream));
+        v.ring_used[b] = 1;
+        AP_TRY(cudaStreamWaitEvent(s, v.ev_prepped[b], 0));
+        const auto &uc = v.stream_cols[(size_t)(c * M + m)];
+        const int t_gram = tr.begin(0, AP_STAGE_GRAM, seq, 0, s);
+        AP_TRY(launch_gram_tc2(v.tmap_hi, v.tmap_lo, v.n, v.d_rs,
+                               v.d_stream_units + uc.first * kOocTileInts, uc.second,
+                               it->d_queue, it->d_status, v.d_g64, out, 0, 1, it->wait_budget_ns,
+                               it->debug, s));
+        tr.end(t_gram, s);
+      }
+    }
+    // the rows' statistics from the chunks' sums, then r from the Gram
+    const int t_fin = tr.begin(0, AP_STAGE_FINALIZE, 0, 0, s);
+    AP_TRY(launch_slice_finalize(v.d_part, v.d_partc, v.n, v.D, v.d_delta_all, v.d_ss, v.d_rs,
+                                 out, s));
+    tr.end(t_fin, s);
+    it->stats.item_loads = v.n;
+    it->stats.reuse_R = 1.0;
+    it->stats.h2d_bytes = (uint64_t)v.n * v.D * 4;
+    it->stats.slot_hit_rate = 1.0;
+    return AP_OK;
+  }
   // three streams: copies (copy_stream) -> pre-processing (prep_stream) ->
   // Gram column m (s), linked by per-slot events
   for (size_t m = 0; m < v.stream_cols.size(); ++m) {

@@ -128,11 +128,14 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
                  float *__restrict__ c32, double *__restrict__ part,
                  double *__restrict__ part_c, int first_chunk,
-                 const int32_t *__restrict__ list) {
+                 const int32_t *__restrict__ list, int64_t col0, int64_t Dl) {
+  // Dp columns (D of them real) of each row go to columns col0.. (a multiple
+  // of 32) of blocked copies Dl columns wide
   __shared__ double2 red[kSplitThreads];
   const int64_t q4 = Dp >> 2;                  // float4 groups per padded row
   const int64_t qf = VEC4 ? (D >> 2) : 0;      // groups wholly inside the row
-  const int64_t nkb_tc = Dp / kTcKBlock, nkb_32 = Dp / kF32KBlock;
+  const int64_t nkb_tc = Dl / kTcKBlock, nkb_32 = Dl / kF32KBlock;
+  const int64_t kb0_tc = col0 / kTcKBlock, kb0_32 = col0 / kF32KBlock;
   const int64_t stq = (int64_t)gridDim.x * blockDim.x;
   const int64_t qa = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   constexpr size_t kTileTc = (size_t)kRowBlock * kTcKBlock, kTile32 = (size_t)kRowBlock * kF32KBlock;
@@ -147,10 +150,10 @@ vec_split_kernel(const float *__restrict__ X, int64_t row0, int64_t out_row0, in
     const float mh = (float)m;
     const float ml = (float)(m - (double)mh);
     const int64_t rb = orow / kRowBlock, ri = orow % kRowBlock;
-    size_t o_tc = ((size_t)rb * nkb_tc + (size_t)(qa >> 3)) * kTileTc + (size_t)ri * kTcKBlock +
-                  4 * (size_t)(qa & 7);
-    size_t o_32 = ((size_t)rb * nkb_32 + (size_t)(qa >> 2)) * kTile32 + (size_t)ri * kF32KBlock +
-                  4 * (size_t)(qa & 3);
+    size_t o_tc = ((size_t)rb * nkb_tc + (size_t)(kb0_tc + (qa >> 3))) * kTileTc +
+                  (size_t)ri * kTcKBlock + 4 * (size_t)(qa & 7);
+    size_t o_32 = ((size_t)rb * nkb_32 + (size_t)(kb0_32 + (qa >> 2))) * kTile32 +
+                  (size_t)ri * kF32KBlock + 4 * (size_t)(qa & 3);
     double acc = 0.0, acc_c = 0.0;
     float psum = 0.f, psum_c = 0.f;
     int64_t q = qa;
@@ -464,11 +467,30 @@ cudaError_t launch_vec_split_slice(const float *X, int64_t row0, int64_t n, int6
   if (vec4)
     vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(
         X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk,
-        nullptr);
+        nullptr, 0, cols_p);
   else
     vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(
         X, row0, row0, n, cols, ld, cols_p, shift, hi, lo, nullptr, part, part_c, first_chunk,
-        nullptr);
+        nullptr, 0, cols_p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vec_split_cols(const float *X, int64_t row0, int64_t n, int64_t cols,
+                                  int64_t ld, int64_t width, int64_t col0, int64_t Dl,
+                                  const double *shift, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                  float *c32, double *part, double *part_c, int first_chunk,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(kSplitParts, (unsigned)(n < 65535 ? n : 65535));
+  const bool vec4 = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  if (vec4)
+    vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, width, shift, hi, lo, c32, part, part_c, first_chunk, nullptr,
+        col0, Dl);
+  else
+    vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(
+        X, row0, row0, n, cols, ld, width, shift, hi, lo, c32, part, part_c, first_chunk, nullptr,
+        col0, Dl);
   return cudaGetLastError();
 }
 
@@ -486,10 +508,10 @@ cudaError_t launch_vec_prep(const float *X, int64_t row0, int64_t out_row0, int6
   auto split = [&](dim3 grid, const int32_t *list) {
     if (vec4)
       vec_split_kernel<true><<<grid, kSplitThreads, 0, s>>>(
-          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list);
+          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list, 0, Dp);
     else
       vec_split_kernel<false><<<grid, kSplitThreads, 0, s>>>(
-          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list);
+          X, row0, out_row0, n, D, ld, Dp, shift, hi, lo, c32, part, part_c, 1, list, 0, Dp);
     return cudaGetLastError();
   };
   const int fg = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);

@@ -281,3 +281,37 @@ def test_pearson_offsets_and_trends(ap, oracle_lib):
         assert it.last_device_error() == 0
     with ap.Items.from_vectors(Xp) as it:
         check(it.load_and_run(Xp).cpu().numpy(), tol, "load and run")
+
+
+@pytest.mark.parametrize("n,D", [(300, (1 << 19) + 77), (513, 3 * (1 << 18) + 40)])
+def test_load_and_run_column_chunks(ap, oracle_lib, n, D):
+    """Rows of 2 MiB and more stream in column chunks of whole 1 MiB pieces
+    (here two and three, the last one ragged), centred on shifts sampled over
+    the whole rows: rows with offsets, trends and periods still match the
+    oracle, and the stored set gives the same correlations afterwards."""
+    X = _offset_trend_rows(n, D, seed=23)
+    Xn = X.numpy()
+    rng = np.random.default_rng(3)
+    pi, pj = oracle_lib.all_pairs(n)
+    keep = rng.choice(len(pi), 1500, replace=False)
+    pi, pj = pi[keep], pj[keep]
+    ref = oracle_lib.pearson(Xn, pi, pj)
+    tol = pearson_tolerance(Xn, pi, pj, 1)
+    p = torch.from_numpy(pi.astype(np.int64) * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
+    Xp = X.pin_memory()
+    with ap.Items.from_vectors(torch.zeros(n, D, device="cuda")) as it:
+        it.set_trace(True)
+        got = it.load_and_run(Xp)
+        tr = it.trace()
+        st = it.stats()
+        again = it.run_pairs()
+        assert it.last_device_error() == 0
+    err = np.abs(got[p].cpu().numpy() - ref)
+    assert np.all(err <= tol), f"max |err| {err.max():.3e}, worst {(err / tol).max():.2f}x"
+    assert np.all(np.abs(got[p].cpu().numpy() - again[p].cpu().numpy())
+                  <= regroup_tolerance(Xn, pi, pj))
+    assert st["h2d_bytes"] == n * D * 4
+    chunks = D // (1 << 18)
+    copies = [e for e in tr if e["stage"] == "copy"]
+    assert len(copies) == chunks * ((n + 255) // 256)
+    assert sum(e["bytes"] for e in copies) == n * D * 4
