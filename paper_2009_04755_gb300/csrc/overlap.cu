@@ -80,7 +80,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 struct TileCtx {
   int32_t i_begin, i_end, j_begin, j_end;
-  int32_t n_rj;          // row jobs in this tile
+  int32_t n_rj;          // row jobs in this tile (partial-sum slots)
+  int32_t n_jobs;        // jobs the units sweep: one row job, or two short ones
   int32_t use_smem;      // J block staged in shared memory
   int64_t j_pt0;         // first storage point of the J block
 };
@@ -120,6 +121,9 @@ __global__ void __launch_bounds__(kThreads)
 overlap_kernel(Params P) {
   constexpr int NV = (MODE == GRAD) ? 4 : 1;     // partial values per (row job, j)
   constexpr int CH = 32 * R;                     // points per chunk
+  // 2-D sets (small items) pair their items' short last chunks; the 3-D
+  // kernel, at R = 4 with items sorted by size, ran 1% slower doing so
+  constexpr bool kMixJobs = DIM == 2;
   extern __shared__ __align__(16) uint8_t smem[];
   float4 *s_pts = reinterpret_cast<float4 *>(smem);
   float *s_lw = reinterpret_cast<float *>(s_pts + P.stage_cap);
@@ -128,8 +132,12 @@ overlap_kernel(Params P) {
   int16_t *s_rj_item = reinterpret_cast<int16_t *>(s_part + P.max_rj * P.part_items * NV);
   int16_t *s_rj_chunk = s_rj_item + kMaxRowJobs;
   int16_t *s_rj_first = s_rj_chunk + kMaxRowJobs;            // [kMaxBlockItems + 1]
+  int16_t *s_job_a = s_rj_first + kMaxBlockItems + 1;         // [kMaxRowJobs] row job
+  int16_t *s_job_b = s_job_a + kMaxRowJobs;                   // [kMaxRowJobs] second, or -1
+  int16_t *s_rem_rj = s_job_b + kMaxRowJobs;                  // [kMaxBlockItems] short last
+  int16_t *s_rem_n = s_rem_rj + kMaxBlockItems;               // chunks and their points
   uint64_t *s_bar = reinterpret_cast<uint64_t *>(
-      (reinterpret_cast<uintptr_t>(s_rj_first + kMaxBlockItems + 1) + 7) & ~uintptr_t(7));
+      (reinterpret_cast<uintptr_t>(s_rem_n + kMaxBlockItems) + 7) & ~uintptr_t(7));
   TileCtx *s_ctx = reinterpret_cast<TileCtx *>(s_bar + 1);
   int *s_tile = reinterpret_cast<int *>(s_ctx + 1);
   int *s_next = s_tile + 1;                      // next (row job, partner) unit
@@ -153,7 +161,12 @@ overlap_kernel(Params P) {
         TileCtx c;
         c.i_begin = P.bstart[IB]; c.i_end = P.bstart[IB + 1];
         c.j_begin = P.bstart[JB]; c.j_end = P.bstart[JB + 1];
-        int nrj = 0;
+        // row jobs (chunks of CH points) in item order, each with its own
+        // partial-sum slot; off the diagonal, items' last chunks short of
+        // CH points are paired into shared jobs (the second item's points
+        // on the lanes after the first one's), longest with shortest
+        const bool mix = kMixJobs && (MODE != COVER) && IB != JB;
+        int nrj = 0, njob = 0, nrem = 0;
         for (int i = c.i_begin; i < c.i_end; ++i) {
           s_rj_first[i - c.i_begin] = (int16_t)nrj;
           const int64_t np = P.cnt[i];
@@ -161,11 +174,32 @@ overlap_kernel(Params P) {
           for (int ch = 0; ch < nch && nrj < P.max_rj; ++ch) {
             s_rj_item[nrj] = (int16_t)(i - c.i_begin);
             s_rj_chunk[nrj] = (int16_t)ch;
+            const int64_t left = np - (int64_t)ch * CH;
+            if (mix && left < CH) {
+              // insertion by point count, most first
+              int k = nrem++;
+              for (; k > 0 && s_rem_n[k - 1] < left; --k) {
+                s_rem_rj[k] = s_rem_rj[k - 1];
+                s_rem_n[k] = s_rem_n[k - 1];
+              }
+              s_rem_rj[k] = (int16_t)nrj;
+              s_rem_n[k] = (int16_t)left;
+            } else {
+              s_job_a[njob] = (int16_t)nrj;
+              s_job_b[njob++] = -1;
+            }
             ++nrj;
           }
         }
+        for (int lo = 0, hi = nrem - 1; lo <= hi;) {
+          s_job_a[njob] = s_rem_rj[lo];
+          if (lo < hi && s_rem_n[lo] + s_rem_n[hi] <= CH) s_job_b[njob++] = s_rem_rj[hi--];
+          else s_job_b[njob++] = -1;
+          ++lo;
+        }
         s_rj_first[c.i_end - c.i_begin] = (int16_t)nrj;
         c.n_rj = nrj;
+        c.n_jobs = njob;
         *s_next = 0;
         c.j_pt0 = P.poff[c.j_begin];
         const int64_t jpts = P.poff[c.j_end] - c.j_pt0;
@@ -257,13 +291,25 @@ overlap_kernel(Params P) {
         int u = 0;
         if (lane == 0) u = atomicAdd(s_next, 1);
         u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= c.n_rj * nJ) break;
-        const int rj = u / nJ, jl = u - rj * nJ;
+        if (u >= c.n_jobs * nJ) break;
+        const int k = u / nJ, jl = u - k * nJ;
+        const int rj = s_job_a[k], rj2 = kMixJobs ? s_job_b[k] : -1;
         const int il = s_rj_item[rj];
         if (diag && jl <= il) continue;
         const int i = c.i_begin + il;
         const int64_t a_begin = P.poff[i] + (int64_t)s_rj_chunk[rj] * CH;
         const int64_t a_end = P.poff[i] + P.cnt[i];
+        // a job of two short chunks: slots [0, nA) hold item i's points,
+        // [nA, nA + n2) those of item i2 (bit r of seg2: a-point r is i2's)
+        const int nA = (int)(a_end - a_begin < CH ? a_end - a_begin : CH);
+        int i2 = i, n2 = 0;
+        int64_t a2_begin = 0;
+        if (rj2 >= 0) {
+          i2 = c.i_begin + s_rj_item[rj2];
+          a2_begin = P.poff[i2] + (int64_t)s_rj_chunk[rj2] * CH;
+          n2 = (int)(P.poff[i2] + P.cnt[i2] - a2_begin);
+        }
+        uint32_t seg2 = 0;
         // this lane's a-points, two per float2 (packed FP32x2 arithmetic);
         // coordinates kept negated so d = b - a is one add, s2k is stored
         // negated; padding and out-of-chunk points get weight 0
@@ -274,8 +320,15 @@ overlap_kernel(Params P) {
           float v[2][5];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int64_t a = a_begin + (2 * p + h) * 32 + lane;
-            if (a < a_end) {
+            const int slot = (2 * p + h) * 32 + lane;
+            int64_t a = a_begin + slot;
+            bool in = slot < nA;
+            if (!in && slot - nA < n2) {
+              a = a2_begin + (slot - nA);
+              in = true;
+              seg2 |= 1u << (2 * p + h);
+            }
+            if (in) {
               const float4 q = __ldg(P.pts + a);
               v[h][0] = q.x; v[h][1] = q.y;
               if (DIM == 3) { v[h][2] = q.z; v[h][3] = q.w; v[h][4] = HAS_W ? exp2f(__ldg(P.lw + a)) : 1.f; }
@@ -297,25 +350,34 @@ overlap_kernel(Params P) {
           const int b0 = (int)(P.poff[j] - c.j_pt0), b1 = b0 + P.cnt[j];
           // -a' = R^T (-(x_a - t)) for this pair's transform
           float2 ntx[R2], nty[R2];
-          float cth = 1.f, sth = 0.f, ttx = 0.f, tty = 0.f;
-          int64_t pidx = 0;
+          // each pair's transform: (i, j), and (i2, j) for i2's a-points
+          float cth[2] = {1.f, 1.f}, sth[2] = {0.f, 0.f}, ttx[2] = {0.f, 0.f}, tty[2] = {0.f, 0.f};
           if (MODE == FWD_T || MODE == GRAD) {
-            const int oi = P.perm[i], oj = P.perm[j];
-            pidx = P.list_mode ? (int64_t)t : pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi, P.n_items);
             const float *pp = (MODE == GRAD && P.params_io) ? P.params_io : P.params;
-            if (pp) {
-              const float th = pp[3 * pidx];
-              ttx = pp[3 * pidx + 1]; tty = pp[3 * pidx + 2];
-              sincosf(th, &sth, &cth);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+              if (g == 1 && rj2 < 0) break;
+              const int oi = P.perm[g ? i2 : i], oj = P.perm[j];
+              const int64_t pidx = P.list_mode ? (int64_t)t
+                                               : pair_index(oi < oj ? oi : oj, oi < oj ? oj : oi,
+                                                            P.n_items);
+              if (pp) {
+                const float th = pp[3 * pidx];
+                ttx[g] = pp[3 * pidx + 1]; tty[g] = pp[3 * pidx + 2];
+                sincosf(th, &sth[g], &cth[g]);
+              }
             }
           }
 #pragma unroll
           for (int p = 0; p < R2; ++p) {
             if (MODE == FWD_T || MODE == GRAD) {
-              const float2 ux = __fadd2_rn(nax[p], make_float2(ttx, ttx));
-              const float2 uy = __fadd2_rn(nay[p], make_float2(tty, tty));
-              ntx[p] = __ffma2_rn(make_float2(cth, cth), ux, __fmul2_rn(make_float2(sth, sth), uy));
-              nty[p] = __ffma2_rn(make_float2(cth, cth), uy, __fmul2_rn(make_float2(-sth, -sth), ux));
+              const bool gx = (seg2 >> (2 * p)) & 1u, gy = (seg2 >> (2 * p + 1)) & 1u;
+              const float2 c2 = make_float2(gx ? cth[1] : cth[0], gy ? cth[1] : cth[0]);
+              const float2 s2 = make_float2(gx ? sth[1] : sth[0], gy ? sth[1] : sth[0]);
+              const float2 ux = __fadd2_rn(nax[p], make_float2(gx ? ttx[1] : ttx[0], gy ? ttx[1] : ttx[0]));
+              const float2 uy = __fadd2_rn(nay[p], make_float2(gx ? tty[1] : tty[0], gy ? tty[1] : tty[0]));
+              ntx[p] = __ffma2_rn(c2, ux, __fmul2_rn(s2, uy));
+              nty[p] = __ffma2_rn(c2, uy, __fmul2_rn(make_float2(-s2.x, -s2.y), ux));
             } else {
               ntx[p] = nax[p]; nty[p] = nay[p];
             }
@@ -465,7 +527,7 @@ overlap_kernel(Params P) {
               }
             };
             if constexpr (SCORE == 0) {
-              if (a_end - a_begin <= 16 * R) sweep(std::integral_constant<int, R / 2>());
+              if (nA + n2 <= 16 * R) sweep(std::integral_constant<int, R / 2>());
               else sweep(std::integral_constant<int, R>());
             } else {
               sweep(std::integral_constant<int, R>());
@@ -483,10 +545,13 @@ overlap_kernel(Params P) {
               }
             }
           }
-          float vF = 0.f, vX = 0.f, vY = 0.f, vT = 0.f;
+          // per a-point terms summed over the warp, into the partial-sum slot
+          // of the a-point's item (two slots for a job of two short chunks)
+          float v[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
           for (int p = 0; p < R2; ++p) {
-            vF = fmaf(aw2[p].x, accF[p].x, fmaf(aw2[p].y, accF[p].y, vF));
+            float tF[2] = {aw2[p].x * accF[p].x, aw2[p].y * accF[p].y};
+            float tX[2] = {0.f, 0.f}, tY[2] = {0.f, 0.f}, tT[2] = {0.f, 0.f};
             if (MODE == GRAD) {
               // with S = sum -e r, Sx = sum -e r x_b, Sy = sum -e r y_b and
               // -a' = (ntx, nty):  sum e r d'   = (Sx + ntx S, Sy + nty S),
@@ -496,24 +561,38 @@ overlap_kernel(Params P) {
               const float2 gy = __ffma2_rn(nty[p], accX[p], accT[p]);
               const float2 gt = __ffma2_rn(nty[p], accY[p],
                                            __fmul2_rn(make_float2(-ntx[p].x, -ntx[p].y), accT[p]));
-              vX = fmaf(aw2[p].x, gx.x, fmaf(aw2[p].y, gx.y, vX));
-              vY = fmaf(aw2[p].x, gy.x, fmaf(aw2[p].y, gy.y, vY));
-              vT = fmaf(aw2[p].x, gt.x, fmaf(aw2[p].y, gt.y, vT));
+              tX[0] = aw2[p].x * gx.x; tX[1] = aw2[p].y * gx.y;
+              tY[0] = aw2[p].x * gy.x; tY[1] = aw2[p].y * gy.y;
+              tT[0] = aw2[p].x * gt.x; tT[1] = aw2[p].y * gt.y;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const bool second = (seg2 >> (2 * p + h)) & 1u;
+              v[0][0] += second ? 0.f : tF[h];
+              v[1][0] += second ? tF[h] : 0.f;
+              if (MODE == GRAD) {
+                v[0][1] += second ? 0.f : tX[h];
+                v[1][1] += second ? tX[h] : 0.f;
+                v[0][2] += second ? 0.f : tY[h];
+                v[1][2] += second ? tY[h] : 0.f;
+                v[0][3] += second ? 0.f : tT[h];
+                v[1][3] += second ? tT[h] : 0.f;
+              }
             }
           }
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            vF += __shfl_xor_sync(0xffffffffu, vF, o);
-            if (MODE == GRAD) {
-              vX += __shfl_xor_sync(0xffffffffu, vX, o);
-              vY += __shfl_xor_sync(0xffffffffu, vY, o);
-              vT += __shfl_xor_sync(0xffffffffu, vT, o);
+          for (int g = 0; g < 2; ++g) {
+            if (g == 1 && rj2 < 0) break;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+              for (int q = 0; q < NV; ++q) v[g][q] += __shfl_xor_sync(0xffffffffu, v[g][q], o);
             }
-          }
-          if (lane == 0) {
-            float *dst = s_part + ((size_t)rj * P.part_items + jl) * NV;
-            dst[0] = vF;
-            if (MODE == GRAD) { dst[1] = vX; dst[2] = vY; dst[3] = vT; }
+            if (lane == 0) {
+              float *dst = s_part + ((size_t)(g ? rj2 : rj) * P.part_items + jl) * NV;
+#pragma unroll
+              for (int q = 0; q < NV; ++q) dst[q] = v[g][q];
+            }
           }
         }
       }
@@ -688,7 +767,7 @@ cudaError_t launch_r(const CloudStore &cs, Params &P, int reg_r, cudaStream_t s)
   constexpr int NV = (MODE == GRAD) ? 4 : 1;
   size_t smem = (size_t)P.stage_cap * 16 + (DIM == 3 ? (size_t)P.stage_cap * 4 : 0) +
                 (size_t)P.max_rj * P.part_items * NV * 4 +
-                (size_t)(3 * kMaxRowJobs + kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
+                (size_t)(4 * kMaxRowJobs + 3 * kMaxBlockItems + 1) * 2 + 16 + sizeof(TileCtx) + 64;
   void (*kern)(Params) = nullptr;
   switch (reg_r) {
     case 2: kern = overlap_kernel<DIM, HAS_W, MODE, 2, SCORE>; break;
