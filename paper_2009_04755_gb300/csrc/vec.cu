@@ -335,8 +335,8 @@ __global__ void pair_correct_kernel(double *__restrict__ out, const double *__re
 
 // ---------------------------------------------------------------------------
 // FP32 CUDA-core Gram over upper-triangle tiles of 128 x 128 items.
-// 256 threads, 8 x 8 outputs per thread, K staged 16 at a time through
-// registers into transposed, double-buffered shared memory.
+// 256 threads, 8 x 8 outputs per thread (FP32x2 FMAs), K staged 16 at a
+// time through registers into transposed, double-buffered shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kF32Tile = 128;
 constexpr int kF32K = 16;
@@ -368,11 +368,13 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
     const float4 *ablk = reinterpret_cast<const float4 *>(C + (size_t)(i0 >> 7) * nkb * 2048);
     const float4 *bblk = reinterpret_cast<const float4 *>(C + (size_t)(j0 >> 7) * nkb * 2048);
 
-    float acc[8][8];
+    // outputs (a, b) as packed pairs over b: one FP32x2 FMA per two outputs,
+    // so the FMA pipe, not the issue slot, bounds the loop
+    float2 acc[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+      for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
 
     float4 ra[2], rb[2];
     auto gload = [&](int kb) {
@@ -405,12 +407,15 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
         float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
         float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
         float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
-        float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                              make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 8; ++a) {
+          const float2 aa = make_float2(av[a], av[a]);
 #pragma unroll
-          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+          for (int b = 0; b < 4; ++b) acc[a][b] = __ffma2_rn(aa, bv[b], acc[a][b]);
+        }
       }
       if (kb + 1 < nk) sstore(buf ^ 1);
       __syncthreads();
@@ -431,7 +436,8 @@ gram_f32_kernel(const float *__restrict__ C, int64_t n, int64_t Dp,
         if (COVER) atomicAdd(reinterpret_cast<int32_t *>(out) + p, 1);
         else
           reinterpret_cast<double *>(out)[p] =
-              ((double)acc[a][b] - (delta ? di * delta[j] : 0.0)) * ri * rs[j];
+              ((double)((b & 1) ? acc[a][b >> 1].y : acc[a][b >> 1].x) -
+               (delta ? di * delta[j] : 0.0)) * ri * rs[j];
       }
     }
   }
