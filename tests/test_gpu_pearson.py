@@ -299,13 +299,18 @@ def test_load_and_run_column_chunks(ap, oracle_lib, n, D):
     tol = pearson_tolerance(Xn, pi, pj, 1)
     p = torch.from_numpy(pi.astype(np.int64) * n - pi * (pi + 1) // 2 + (pj - pi - 1)).cuda()
     Xp = X.pin_memory()
-    with ap.Items.from_vectors(torch.zeros(n, D, device="cuda")) as it:
+    both = (ap.AP_PREC_SPLIT_BF16, ap.AP_PREC_FP32)
+    with ap.Items.from_vectors(torch.zeros(n, D, device="cuda"), precisions=both) as it:
         it.set_trace(True)
         got = it.load_and_run(Xp)
         tr = it.trace()
         st = it.stats()
         again = it.run_pairs()
+        # the FP32 copy written chunk by chunk beside the split one
+        got32 = it.run_pairs(ap.AP_FN_PEARSON, ap.AP_PREC_FP32)[p].cpu().numpy()
         assert it.last_device_error() == 0
+    err32 = np.abs(got32 - ref)
+    assert np.all(err32 <= pearson_tolerance(Xn, pi, pj, 0)), float(err32.max())
     err = np.abs(got[p].cpu().numpy() - ref)
     assert np.all(err <= tol), f"max |err| {err.max():.3e}, worst {(err / tol).max():.2f}x"
     assert np.all(np.abs(got[p].cpu().numpy() - again[p].cpu().numpy())
