@@ -244,8 +244,9 @@ namespace ap {
 // chunks of kSparseChunk codes; cptr[c][i] = first entry of row i with a
 // code >= c * kSparseChunk, relative to the row's start (chunk-major, so the
 // bounds of 32 consecutive rows in one chunk are one coalesced load)
-constexpr int kSparseChunk = 2048;
-constexpr int kSparseBlock = 32;
+constexpr int kSparseChunk = 4096;
+constexpr int kSparseBlock = 32;     // items i of a tile
+constexpr int kSparseBlockJ = 64;    // items j of a tile
 struct SparseStore {
   int64_t n = 0, dim = 0, nnz = 0, n_chunks = 0;
   int64_t *d_off = nullptr;

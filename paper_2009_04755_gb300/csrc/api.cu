@@ -471,7 +471,8 @@ ap_status ap_run_pairs(ap_items *it, int32_t fn, int32_t precision, const float 
   if (it->kind == AP_ITEMS_SPARSE) {
     AP_TRY(launch_sparse_cosine(it->sp, reinterpret_cast<double *>(out), cover, it->d_queue, s));
     it->stats.tiles = it->sp.n_tiles;
-    it->stats.tile_m = it->stats.tile_n = kSparseBlock;
+    it->stats.tile_m = kSparseBlock;
+    it->stats.tile_n = kSparseBlockJ;
     it->stats.item_loads = it->sp.n;
     it->stats.reuse_R = 1.0;
     it->stats.slot_hit_rate = 1.0;

@@ -6,25 +6,25 @@
 //
 // Rows are CSR (strictly increasing int32 codes, FP32 values) over an index
 // space of `dim` codes (20^k k-mers), cut into chunks of kSparseChunk codes.
-// Schedule: persistent CTAs pop tiles (a block of 32 items I x a block of 32
-// items J, upper triangle in recursive quadrant order, Sec. IV-B) from an
-// atomic queue.  The 16 warps walk the chunks together, for half of I (16
-// rows) at a time: per chunk each warp scatters one row i into the dense
-// form of the chunk in shared memory, and after a barrier every lane reads
-// its share of the chunk's entries of the warp's two rows j (once, into
-// registers) and multiplies each against the 16 rows i.  The dense form is
-// code-major, the 16 rows' values of one code side by side (64 bytes), so
-// one 16-byte load gathers four rows; the four 16-byte groups of a code are
-// XOR-swizzled by code bits 1-2, which spreads the loads of random codes
-// over all eight 16-byte bank groups.
+// Schedule: persistent CTAs pop tiles (a block of 32 items I x a block of 64
+// items J, every block pair holding a pair i < j, Sec. IV-B) from an atomic
+// queue.  The 16 warps walk the chunks together, for 8 rows of I at a time:
+// per chunk warps 0-7 each scatter one row i into the dense form of the
+// chunk in shared memory, and after a barrier every lane reads its share of
+// the chunk's entries of the warp's four rows j (once, into registers) and
+// multiplies each against the 8 rows i.  The dense form is code-major, the 8
+// rows' values of one code side by side (32 bytes), so one 16-byte load
+// gathers four rows; the two 16-byte groups of a code are XOR-swizzled by
+// code bit 1, which spreads the loads of random codes over the bank groups.
 // The barriers pace every chunk step by its busiest warp, so the rows j of a
-// block are dealt to the warps in pairs of one heavy and one light row (by
-// entry count).  Each warp copies the next chunk's entries of its rows (up to
-// 64 per row)
-// into a two-stage shared-memory ring with cp.async while it works on the
-// current one, so the chunk loop does not wait on DRAM.  Per lane the FP32
-// products are summed over up to 64 chunks, then folded into FP64 pair sums
-// in shared memory.
+// block are dealt to the warps by entry count in a snake (heavy and light
+// rows alternate).  Each warp copies the next chunk's entries of its rows (up
+// to 64 per row) into a two-stage shared-memory ring with cp.async while it
+// works on the current one, so the chunk loop does not wait on DRAM.  Per
+// lane the FP32 products are summed over up to 64 chunks, then folded into
+// FP64 pair sums in shared memory.  (Tiles of 32 x 32 items with 16 rows i
+// per pass over chunks of 2048 codes ran 2.99 s on the 2500-item set, these
+// 2.89 s: the lookups, not the chunk steps, set the pace.)
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,18 +38,20 @@ namespace ap {
 
 namespace {
 
-constexpr int kWarps = 16;                   // rows i per pass (one dense array each)
+constexpr int kWarps = 16;                   // warps per CTA
 constexpr int kThreads = 32 * kWarps;
-constexpr int B = kSparseBlock;
-constexpr int kJ = B / kWarps;               // rows j per warp
-constexpr int kMinBlocks = 16 / kWarps;      // CTAs per SM the registers are sized for
+constexpr int kRows = 8;                     // rows i per pass: the dense form's rows
+constexpr int kGroups = kRows / 4;           // 16-byte groups of a code in the dense form
+constexpr int BI = kSparseBlock;             // items i of a tile
+constexpr int BJ = kSparseBlockJ;            // items j of a tile
+constexpr int kJ = BJ / kWarps;              // rows j per warp
 constexpr int kStage = 64;                   // staged entries per row and chunk
 constexpr int W = kSparseChunk;
 constexpr int kFoldChunks = 64;
 
-// word of row q (0..kWarps-1) at chunk code k in the swizzled dense form
+// word of row q (0..kRows-1) at chunk code k in the swizzled dense form
 __device__ __forceinline__ int dense_at(int k, int q) {
-  return k * kWarps + ((((q >> 2) ^ (k >> 1)) & 3) << 2) + (q & 3);
+  return k * kRows + ((((q >> 2) ^ (k >> 1)) & (kGroups - 1)) << 2) + (q & 3);
 }
 
 // asynchronous 4-byte copy global -> shared; src_bytes 0 writes zeros and
@@ -68,26 +70,31 @@ __device__ __forceinline__ void cp_async_wait_prev() {
 }
 
 // One warp's staging of a chunk: up to kStage entries (2 per lane) of its row
-// i and of its kJ rows j, filled by cp.async one chunk ahead.
+// i (dense-row owners) and of its kJ rows j, filled by cp.async one chunk
+// ahead.
 struct WarpStage {
   int32_t code[1 + kJ][kStage];
   float val[1 + kJ][kStage];
 };
 
 template <int COVER>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+__global__ void __launch_bounds__(kThreads, 1)
 sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ idx,
                   const float *__restrict__ val, const int32_t *__restrict__ cptr,
                   const double *__restrict__ rs, int64_t n, int64_t n_chunks,
                   const int32_t *__restrict__ tiles, int64_t n_tiles,
                   const int32_t *__restrict__ jperm, int32_t *queue, void *out) {
   extern __shared__ __align__(16) uint8_t smem[];
-  float *dense = reinterpret_cast<float *>(smem);                     // [W][kWarps], swizzled
-  double *s_g = reinterpret_cast<double *>(dense + kWarps * W);       // [B][B]
-  WarpStage *stage = reinterpret_cast<WarpStage *>(s_g + B * B);      // [kWarps][2]
+  float *dense = reinterpret_cast<float *>(smem);                     // [W][kRows], swizzled
+  double *s_g = reinterpret_cast<double *>(dense + kRows * W);        // [BI][BJ]
+  WarpStage *stage = reinterpret_cast<WarpStage *>(s_g + BI * BJ);    // [kWarps][2]
   __shared__ int s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x; k < kWarps * W; k += kThreads) dense[k] = 0.f;
+  // warps 0..kRows-1 each own one dense row (scatter and clear it, so the
+  // clearing of a chunk and the next chunk's scatter stay in program order)
+  const int wr = warp % kRows;
+  const bool owner = warp < kRows;
+  for (int k = threadIdx.x; k < kRows * W; k += kThreads) dense[k] = 0.f;
   WarpStage *my_stage = stage + warp * 2;
 
   for (;;) {
@@ -95,43 +102,39 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
     __syncthreads();
     const int64_t t = s_tile;
     if (t >= n_tiles) break;
-    const int64_t I = tiles[2 * t], J = tiles[2 * t + 1];
-    const int64_t i0 = I * B, j0 = J * B;
-    const int32_t *jslot = jperm + J * B;     // item of each row slot of J
-    const bool diag = I == J;
-    for (int q = threadIdx.x; q < B * B; q += kThreads) s_g[q] = 0.0;
+    const int64_t i0 = (int64_t)tiles[2 * t] * BI, j0 = (int64_t)tiles[2 * t + 1] * BJ;
+    const int32_t *jslot = jperm + (int64_t)tiles[2 * t + 1] * BJ;   // item of each row slot of J
+    for (int q = threadIdx.x; q < BI * BJ; q += kThreads) s_g[q] = 0.0;
     __syncthreads();
 
     if (!COVER) {
-      for (int pass = 0; pass < B / kWarps; ++pass) {
-        // the warp's rows: r = 0 its row i (scattered into dense[warp]),
-        // r = 1.. its rows j (slots warp + (r - 1) * kWarps, items jl)
+      for (int pass = 0; pass < BI / kRows; ++pass) {
+        // the warp's rows: r = 0 its row i (owners only: dense row wr),
+        // r = 1.. its rows j (slots warp + (r - 1) * kWarps)
         int64_t row[1 + kJ], base[1 + kJ];
-        int32_t jl[kJ];
         bool valid[1 + kJ];
-        row[0] = i0 + pass * kWarps + warp;
+        row[0] = i0 + pass * kRows + wr;
 #pragma unroll
-        for (int h = 0; h < kJ; ++h) {
-          jl[h] = jslot[warp + h * kWarps];
-          row[1 + h] = j0 + jl[h];
-        }
+        for (int h = 0; h < kJ; ++h) row[1 + h] = j0 + jslot[warp + h * kWarps];
+        // pairs need j > i: a row j at or before every row i of the pass has none
+        const int64_t i_first = i0 + pass * kRows;
 #pragma unroll
         for (int r = 0; r <= kJ; ++r) {
-          valid[r] = row[r] < n;
+          valid[r] = row[r] < n && (r == 0 ? owner : row[r] > i_first);
           base[r] = valid[r] ? off[row[r]] : 0;
         }
-        float acc[kJ][kWarps];
+        float acc[kJ][kRows];
 #pragma unroll
         for (int h = 0; h < kJ; ++h)
 #pragma unroll
-          for (int q = 0; q < kWarps; ++q) acc[h][q] = 0.f;
-        // one entry (code k of the chunk, value v) of a row j against the 16
-        // rows i: four 16-byte loads of the dense form
-        auto product = [&](int32_t k, float v, float (&a)[kWarps]) {
-          const float4 *dk = reinterpret_cast<const float4 *>(dense + k * kWarps);
+          for (int q = 0; q < kRows; ++q) acc[h][q] = 0.f;
+        // one entry (code k of the chunk, value v) of a row j against the
+        // kRows rows i: kGroups 16-byte loads of the dense form
+        auto product = [&](int32_t k, float v, float (&a)[kRows]) {
+          const float4 *dk = reinterpret_cast<const float4 *>(dense + k * kRows);
 #pragma unroll
-          for (int g = 0; g < kWarps / 4; ++g) {
-            const float4 d = dk[(g ^ (k >> 1)) & 3];
+          for (int g = 0; g < kGroups; ++g) {
+            const float4 d = dk[(g ^ (k >> 1)) & (kGroups - 1)];
             a[4 * g + 0] = fmaf(d.x, v, a[4 * g + 0]);
             a[4 * g + 1] = fmaf(d.y, v, a[4 * g + 1]);
             a[4 * g + 2] = fmaf(d.z, v, a[4 * g + 2]);
@@ -182,19 +185,17 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
 #pragma unroll
           for (int u = 0; u < kStage / 32; ++u)
             if (u * 32 + lane < ni)
-              dense[dense_at(st.code[0][u * 32 + lane] - code0, warp)] = st.val[0][u * 32 + lane];
+              dense[dense_at(st.code[0][u * 32 + lane] - code0, wr)] = st.val[0][u * 32 + lane];
           for (int32_t e = kStage + lane; e < ni; e += 32) {
             const int64_t g = base[0] + b0[0] + e;
-            dense[dense_at(__ldg(idx + g) - code0, warp)] = __ldg(val + g);
+            dense[dense_at(__ldg(idx + g) - code0, wr)] = __ldg(val + g);
           }
           __syncthreads();
           // every entry of the warp's rows j in this chunk against the
-          // kWarps rows i held in the dense arrays
+          // kRows rows i held in the dense arrays
 #pragma unroll
           for (int h = 0; h < kJ; ++h) {
-            // on the diagonal, rows j at or before every row i of this pass
-            // have no pair i < j here
-            if (!valid[1 + h] || (diag && jl[h] <= pass * kWarps)) continue;
+            if (!valid[1 + h]) continue;
             const int32_t nj = b1[1 + h] - b0[1 + h];
 #pragma unroll
             for (int u = 0; u < kStage / 32; ++u) {
@@ -210,9 +211,9 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
           __syncthreads();
 #pragma unroll
           for (int u = 0; u < kStage / 32; ++u)
-            if (u * 32 + lane < ni) dense[dense_at(st.code[0][u * 32 + lane] - code0, warp)] = 0.f;
+            if (u * 32 + lane < ni) dense[dense_at(st.code[0][u * 32 + lane] - code0, wr)] = 0.f;
           for (int32_t e = kStage + lane; e < ni; e += 32)
-            dense[dense_at(__ldg(idx + base[0] + b0[0] + e) - code0, warp)] = 0.f;
+            dense[dense_at(__ldg(idx + base[0] + b0[0] + e) - code0, wr)] = 0.f;
 #pragma unroll
           for (int r = 0; r <= kJ; ++r) { b0[r] = b1[r]; b1[r] = b2[r]; b2[r] = b3[r]; }
           if (++since == kFoldChunks || c + 1 == n_chunks) {
@@ -221,10 +222,10 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
 #pragma unroll
             for (int h = 0; h < kJ; ++h)
 #pragma unroll
-              for (int q = 0; q < kWarps; ++q) {
+              for (int q = 0; q < kRows; ++q) {
                 double v = (double)acc[h][q];
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) s_g[(pass * kWarps + q) * B + warp + h * kWarps] += v;
+                if (lane == 0) s_g[(pass * kRows + q) * BJ + warp + h * kWarps] += v;
                 acc[h][q] = 0.f;
               }
           }
@@ -233,8 +234,8 @@ sparse_cos_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ i
       }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < B * B; q += kThreads) {
-      const int il = q / B, slot = q - il * B;
+    for (int q = threadIdx.x; q < BI * BJ; q += kThreads) {
+      const int il = q / BJ, slot = q - il * BJ;
       const int64_t i = i0 + il, j = j0 + jslot[slot];
       if (i >= n || j >= n || j <= i) continue;
       const int64_t p = pair_index(i, j, n);
@@ -336,28 +337,34 @@ ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
     sparse_cptr_kernel<<<g2, 256, 0, s>>>(sp.d_off, sp.d_idx, sp.n, sp.n_chunks, sp.d_cptr);
     AP_TRY(cudaGetLastError());
   }
-  // row slots of each block: by entry count, slot w takes the w-th heaviest
-  // row and slot w + 16 the w-th lightest (rows past n count as empty)
-  const int64_t nblk = (sp.n + kSparseBlock - 1) / kSparseBlock;
-  std::vector<int32_t> jperm((size_t)std::max<int64_t>(nblk, 1) * kSparseBlock);
-  for (int64_t b = 0; b < nblk; ++b) {
-    int32_t order[kSparseBlock];
+  // row slots of each J block of BJ items, dealt to the warps by entry
+  // count in a snake (warp w takes slots w, w + kWarps, ...: the w-th
+  // heaviest row, the w-th lightest of the next kWarps, ...), so every
+  // warp's rows j weigh about the same (rows past n count as empty)
+  const int64_t nbi = (sp.n + BI - 1) / BI, nbj = (sp.n + BJ - 1) / BJ;
+  std::vector<int32_t> jperm((size_t)std::max<int64_t>(nbj, 1) * BJ);
+  for (int64_t b = 0; b < nbj; ++b) {
+    int32_t order[BJ];
     auto cnt = [&](int32_t l) {
-      const int64_t i = b * kSparseBlock + l;
+      const int64_t i = b * BJ + l;
       return i < sp.n ? off[i + 1] - off[i] : (int64_t)-1;
     };
-    for (int32_t l = 0; l < kSparseBlock; ++l) order[l] = l;
-    std::stable_sort(order, order + kSparseBlock,
-                     [&](int32_t a, int32_t c) { return cnt(a) > cnt(c); });
-    for (int w = 0; w < kWarps; ++w) {
-      jperm[(size_t)b * kSparseBlock + w] = order[w];
-      jperm[(size_t)b * kSparseBlock + w + kWarps] = order[kSparseBlock - 1 - w];
-    }
+    for (int32_t l = 0; l < BJ; ++l) order[l] = l;
+    std::stable_sort(order, order + BJ, [&](int32_t a, int32_t c) { return cnt(a) > cnt(c); });
+    for (int h = 0; h < kJ; ++h)
+      for (int w = 0; w < kWarps; ++w)
+        jperm[(size_t)b * BJ + w + h * kWarps] = order[h * kWarps + ((h & 1) ? kWarps - 1 - w : w)];
   }
   AP_TRY(dmalloc(&sp.d_jperm, jperm.size()));
   AP_TRY(cudaMemcpyAsync(sp.d_jperm, jperm.data(), jperm.size() * 4, cudaMemcpyHostToDevice, s));
+  // tiles (I block of BI items, J block of BJ items) holding a pair i < j,
+  // the J blocks in order and within each its I blocks
   std::vector<int32_t> tiles;
-  dc_block_pairs(nblk, tiles);
+  for (int64_t bj = 0; bj < nbj; ++bj)
+    for (int64_t bi = 0; bi < nbi && bi * BI < (bj + 1) * BJ - 1; ++bi) {
+      tiles.push_back((int32_t)bi);
+      tiles.push_back((int32_t)bj);
+    }
   sp.n_tiles = (int64_t)tiles.size() / 2;
   AP_TRY(dmalloc(&sp.d_tiles, std::max<size_t>(tiles.size(), 2)));
   if (!tiles.empty())
@@ -367,14 +374,15 @@ ap_status create_sparse(const ap_items_desc *d, ap_items *it, cudaStream_t s) {
   AP_TRY(cudaStreamSynchronize(s));
   if (bad) return AP_ERR_INVALID_ARG;
   it->stats.tiles = sp.n_tiles;
-  it->stats.tile_m = it->stats.tile_n = kSparseBlock;
+  it->stats.tile_m = BI;
+  it->stats.tile_n = BJ;
   return AP_OK;
 }
 
 cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverage,
                                  int32_t *queue, cudaStream_t s) {
   if (sp.n_tiles <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kWarps * W * 4 + (size_t)B * B * 8 +
+  const size_t smem = (size_t)kRows * W * 4 + (size_t)BI * BJ * 8 +
                       (size_t)kWarps * 2 * sizeof(WarpStage);
   void (*kern)(const int64_t *, const int32_t *, const float *, const int32_t *, const double *,
                int64_t, int64_t, const int32_t *, int64_t, const int32_t *, int32_t *, void *) =
@@ -383,7 +391,7 @@ cudaError_t launch_sparse_cosine(const SparseStore &sp, double *out, int coverag
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>((int64_t)num_sms() * kMinBlocks, sp.n_tiles);
+  const int64_t grid = std::min<int64_t>((int64_t)num_sms(), sp.n_tiles);
   kern<<<(int)grid, kThreads, smem, s>>>(sp.d_off, sp.d_idx, sp.d_val, sp.d_cptr, sp.d_rs, sp.n,
                                          sp.n_chunks, sp.d_tiles, sp.n_tiles, sp.d_jperm, queue,
                                          out);

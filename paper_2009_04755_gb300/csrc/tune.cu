@@ -103,7 +103,8 @@ extern "C" ap_status ap_get_plan(const ap_items *it, ap_plan *out) {
   out->k_split = 0;
   out->mma_ctas = 0;
   if (it->kind == AP_ITEMS_SPARSE) {
-    out->block_items = out->block_pts = kSparseBlock;
+    out->block_items = kSparseBlock;       // items i of a tile (j: kSparseBlockJ)
+    out->block_pts = kSparseBlockJ;
     out->reg_r = out->sorted = 0;
     out->rate = 0.0;
     return AP_OK;
