@@ -135,12 +135,13 @@ def test_autograd_list(ap, oracle_lib):
 
 
 @pytest.mark.parametrize("prec", [1, 0])
-@pytest.mark.parametrize("m", [2000, 40])
-def test_pearson_list(ap, oracle_lib, prec, m):
+@pytest.mark.parametrize("m,D", [(2000, 12325), (40, 12325), (500, 50)])
+def test_pearson_list(ap, oracle_lib, prec, m, D):
     """2000 pairs over three row blocks read a row-major copy of the rows
     (the last 128-column group holds 64, the last block 44 rows); 40 pairs
-    read the blocked arrays in place."""
-    n, D = 300, 12325
+    read the blocked arrays in place; rows of 50 values are one 64-column
+    group of the copy."""
+    n = 300
     X = synth.vectors_grouped(n, D, seed=31) + torch.linspace(-5, 5, n)[:, None]
     X = X.contiguous()
     pi, pj = _random_list(n, m, seed=prec)
