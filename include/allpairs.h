@@ -265,6 +265,11 @@ ap_status ap_run_pairs(ap_items *items, int32_t fn, int32_t precision,
  *   fn = AP_FN_PEARSON: resident vector sets; out device double[n_pairs];
  *        precision selects the representation (built at creation); one warp
  *        per pair, the Gram's three products per column in FP32, FP64 sums.
+ *        A list of at least 32 pairs per 128-item row block it touches first
+ *        copies those blocks into row-major rows of one 4-byte word per
+ *        column, in a buffer of n_items x dim words (padded to 64) that the
+ *        first such call allocates and the handle keeps until ap_destroy;
+ *        where that allocation fails, the call reads the blocked rows.
  *   fn = AP_FN_COSINE: sparse sets; out device double[n_pairs]; the two
  *        rows' codes merged (FP32 products, FP64 sums).
  * Errors: AP_ERR_INVALID_ARG (fn/kind mismatch, an index out of range or a
